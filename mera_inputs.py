@@ -1,0 +1,82 @@
+"""Seeded synthetic inputs shared by the CUDA path, the tests and the oracle.
+
+This module draws random numbers and shapes them into valid inputs: it holds
+none of the MERA arithmetic (no superoperator, environment, update or
+Hamiltonian).  Both sides receive the very same arrays, so the sign convention
+of the QR factorisation used to make isometries is irrelevant to parity.
+
+Tensor conventions (real arithmetic, row-major):
+
+* isometry   w[a, b, c]      : a, b lower (fine) legs, c upper (coarse) leg,
+                                sum_ab w[a,b,c] w[a,b,c'] = delta_cc'   (Eq. iso)
+* disentangler u[a, b, m, n] : a, b lower legs, m, n upper legs,
+                                sum_ab u[a,b,m,n] u[a,b,m',n'] = delta delta (Eq. unitarity)
+* 3-site operator X[i1,i2,i3, j1,j2,j3]: ket legs first, then bra legs.
+
+Layer dimensions follow the scale-invariant MERA of Sec. II A with tau* = 3:
+two transitional layers and one scale-invariant layer.  The physical sites are
+spins blocked in pairs (local dimension 4); the first layer maps 4 -> min(16, chi),
+the second min(16, chi) -> chi, the scale-invariant layer chi -> chi.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+D_PHYS = 4  # two spin-1/2 sites blocked into one site
+
+
+def layer_dims(chi: int, n_layers: int = 3, d: int = D_PHYS) -> list[tuple[int, int]]:
+    """(chi_bottom, chi_top) of every layer, bottom layer first."""
+    dims = []
+    bottom = d
+    for tau in range(n_layers):
+        top = min(bottom * bottom, chi)
+        dims.append((bottom, top))
+        bottom = top
+    return dims
+
+
+def random_isometry(rng: np.random.Generator, rows: int, cols: int) -> np.ndarray:
+    """Orthonormal columns from the QR factorisation of an N(0,1) matrix."""
+    if cols > rows:
+        raise ValueError("an isometry needs rows >= cols")
+    g = rng.standard_normal((rows, cols))
+    q, _ = np.linalg.qr(g)
+    return np.ascontiguousarray(q[:, :cols])
+
+
+def random_w(rng: np.random.Generator, chi_b: int, chi_t: int) -> np.ndarray:
+    return random_isometry(rng, chi_b * chi_b, chi_t).reshape(chi_b, chi_b, chi_t)
+
+
+def random_u(rng: np.random.Generator, chi_b: int) -> np.ndarray:
+    return random_isometry(rng, chi_b * chi_b, chi_b * chi_b).reshape(chi_b, chi_b, chi_b, chi_b)
+
+
+def init_mera(seed: int, chi: int, n_layers: int = 3, d: int = D_PHYS):
+    """Seeded initial tensors: list of (u, w) per layer, bottom layer first."""
+    rng = np.random.default_rng(seed)
+    layers = []
+    for chi_b, chi_t in layer_dims(chi, n_layers, d):
+        u = random_u(rng, chi_b)
+        w = random_w(rng, chi_b, chi_t)
+        layers.append((u, w))
+    return layers
+
+
+def random_operator(rng: np.random.Generator, chi: int, symmetric: bool = True) -> np.ndarray:
+    """A random 3-site operator (chi^3 x chi^3), optionally symmetric."""
+    n = chi ** 3
+    x = rng.standard_normal((n, n))
+    if symmetric:
+        x = 0.5 * (x + x.T)
+    return x.reshape((chi,) * 6)
+
+
+def random_density(rng: np.random.Generator, chi: int) -> np.ndarray:
+    """A random 3-site density matrix: symmetric, positive semidefinite, unit trace."""
+    n = chi ** 3
+    g = rng.standard_normal((n, n))
+    r = g @ g.T
+    r /= np.trace(r)
+    return r.reshape((chi,) * 6)

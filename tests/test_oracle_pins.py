@@ -1,0 +1,327 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each test uses an independent
+construction (dense lattice operators, Kronecker products, finite
+differences, closed forms, exact invariants) chosen so that a dropped term,
+a wrong sign, a swapped leg or a transposed operand in the oracle fails one
+of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import mera_inputs as I
+from oracle import mera_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+
+
+def _mat(x):
+    n = int(round(x.size ** 0.5))
+    return x.reshape(n, n)
+
+
+def _rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+# --------------------------------------------------------------------------
+# Hamiltonian: blocked 3-site densities sum to the dense spin Hamiltonian.
+# --------------------------------------------------------------------------
+def _embed(op, sites, nsites, d):
+    """Dense operator on nsites sites (dim d each) acting as `op` on `sites`."""
+    k = len(sites)
+    t = op.reshape((d,) * (2 * k))
+    rest = [s for s in range(nsites) if s not in sites]
+    eye = np.eye(d ** len(rest)).reshape((d,) * (2 * len(rest)))
+    full = np.tensordot(t, eye, axes=0)  # legs: op ket, op bra, rest ket, rest bra
+    ket_order = list(sites) + rest
+    # full legs are [op kets (k), op bras (k), rest kets, rest bras]
+    n_rest = len(rest)
+    src_ket = list(range(k)) + list(range(2 * k, 2 * k + n_rest))
+    src_bra = list(range(k, 2 * k)) + list(range(2 * k + n_rest, 2 * k + 2 * n_rest))
+    perm_ket = [src_ket[ket_order.index(s)] for s in range(nsites)]
+    perm_bra = [src_bra[ket_order.index(s)] for s in range(nsites)]
+    return np.transpose(full, perm_ket + perm_bra).reshape(d ** nsites, d ** nsites)
+
+
+def _dense_ising_ring(nspins, hz):
+    x = np.array([[0.0, 1.0], [1.0, 0.0]])
+    z = np.array([[1.0, 0.0], [0.0, -1.0]])
+    h = np.zeros((2 ** nspins, 2 ** nspins))
+    for n in range(nspins):
+        h -= _embed(np.kron(x, x), [n, (n + 1) % nspins], nspins, 2)
+        h -= hz * _embed(z, [n], nspins, 2)
+    return h
+
+
+@pytest.mark.parametrize("nblocks", [3, 4])
+@pytest.mark.parametrize("hz", [1.0, 0.7])
+def test_blocked_density_sums_to_dense_hamiltonian(nblocks, hz):
+    h3 = O.three_site_density(O.blocked_two_site(hz))
+    total = np.zeros((4 ** nblocks, 4 ** nblocks))
+    for j in range(nblocks):
+        total += _embed(h3, [j, (j + 1) % nblocks, (j + 2) % nblocks], nblocks, 4)
+    dense = _dense_ising_ring(2 * nblocks, hz)  # block j = spins (2j, 2j+1)
+    assert np.abs(total - dense).max() < 1e-13
+
+
+def test_shifted_density_is_negative_semidefinite():
+    h1, s = O.ising_h1(1.0)
+    ev = np.linalg.eigvalsh(_mat(h1))
+    assert ev.max() == pytest.approx(0.0, abs=1e-13)
+    h3 = O.three_site_density(O.blocked_two_site(1.0))
+    assert np.abs(_mat(h1) + s * np.eye(64) - h3).max() < 1e-15
+
+
+def test_exact_energy_closed_form():
+    gold = json.load(open(GOLDEN))
+    assert O.exact_energy_per_spin(1.0) == pytest.approx(gold["e_exact_per_spin"]["value"], abs=1e-15)
+    assert O.exact_energy_per_spin(1.0) == pytest.approx(-4.0 / np.pi, abs=1e-15)
+
+
+def test_exact_energy_off_critical_against_exact_diagonalisation():
+    """Gapped chain (h = 3): a 12-spin ring has the infinite-chain energy
+    density up to exponentially small finite-size corrections."""
+    from scipy.sparse.linalg import eigsh
+
+    hz, n = 3.0, 12
+    h = _dense_ising_ring(n, hz)
+    e0 = eigsh(h, k=1, which="SA")[0][0] / n
+    assert O.exact_energy_per_spin(hz) == pytest.approx(e0, abs=3e-7)
+
+
+# --------------------------------------------------------------------------
+# Superoperators: invariants.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("chi_b,chi_t", [(2, 2), (3, 3), (2, 3), (4, 3)])
+def test_ascend_identity_is_identity(chi_b, chi_t):
+    rng = _rng(1)
+    u, w = I.random_u(rng, chi_b), I.random_w(rng, chi_b, chi_t)
+    eye_b = np.eye(chi_b ** 3).reshape((chi_b,) * 6)
+    a = O.ascend(eye_b, u, w)
+    assert np.abs(_mat(a) - np.eye(chi_t ** 3)).max() < 1e-13
+    for case in ("even", "odd"):
+        assert np.abs(_mat(O.ascend_case(eye_b, u, w, case)) - np.eye(chi_t ** 3)).max() < 1e-13
+
+
+@pytest.mark.parametrize("chi_b,chi_t", [(2, 2), (3, 3), (2, 3)])
+def test_duality_ascend_descend(chi_b, chi_t):
+    rng = _rng(2)
+    u, w = I.random_u(rng, chi_b), I.random_w(rng, chi_b, chi_t)
+    h = I.random_operator(rng, chi_b, symmetric=False)
+    rho = I.random_operator(rng, chi_t, symmetric=False)
+    for case in ("even", "odd"):
+        lhs = np.sum(O.ascend_case(h, u, w, case) * rho)
+        rhs = np.sum(h * O.descend_case(rho, u, w, case))
+        assert abs(lhs - rhs) <= 1e-13 * max(1.0, abs(lhs))
+
+
+@pytest.mark.parametrize("chi", [2, 3])
+def test_descend_preserves_trace_and_positivity(chi):
+    rng = _rng(3)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    rho = I.random_density(rng, chi)
+    d = _mat(O.descend(rho, u, w))
+    assert np.trace(d) == pytest.approx(1.0, abs=1e-14)
+    assert np.abs(d - d.T).max() < 1e-14
+    assert np.linalg.eigvalsh(d).min() > -1e-14
+
+
+def test_mirror_symmetry_even_odd():
+    """Reflecting the lattice maps the even causal-cone position to the odd one."""
+    rng = _rng(4)
+    chi = 3
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    h = I.random_operator(rng, chi, symmetric=False)
+    um = np.transpose(u, (1, 0, 3, 2))
+    wm = np.transpose(w, (1, 0, 2))
+    rev = (2, 1, 0, 5, 4, 3)
+    lhs = O.ascend_case(h, u, w, "odd")
+    rhs = np.transpose(O.ascend_case(np.transpose(h, rev), um, wm, "even"), rev)
+    assert np.abs(lhs - rhs).max() < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Dense brute force on a 6-site periodic chain.
+# --------------------------------------------------------------------------
+def _layer_matrix(u, w):
+    """M = (u_12 u_34 u_50)(w_01 w_23 w_45): fine 6-site space <- coarse 3 sites."""
+    chi_b, chi_t = w.shape[0], w.shape[2]
+    # U[f0..f5, m0..m5] with disentanglers on fine pairs (1,2), (3,4), (5,0)
+    U = np.einsum("bcBC,deDE,faFA->abcdefABCDEF", u, u, u)
+    W = np.einsum("ABx,CDy,EFz->ABCDEFxyz", w, w, w)
+    M = np.tensordot(U, W, axes=([6, 7, 8, 9, 10, 11], [0, 1, 2, 3, 4, 5]))
+    return M.reshape(chi_b ** 6, chi_t ** 3)
+
+
+@pytest.mark.parametrize("chi_b,chi_t", [(2, 2), (2, 3)])
+def test_brute_force_six_site_ring(chi_b, chi_t):
+    rng = _rng(5)
+    u, w = I.random_u(rng, chi_b), I.random_w(rng, chi_b, chi_t)
+    M = _layer_matrix(u, w)
+    assert np.abs(M.T @ M - np.eye(chi_t ** 3)).max() < 1e-13
+    h = I.random_operator(rng, chi_b, symmetric=False)
+    hm = _mat(h)
+    for case, sites, coarse_order in (("even", [0, 1, 2], (2, 0, 1)), ("odd", [1, 2, 3], (0, 1, 2))):
+        dense = M.T @ _embed(hm, sites, 6, chi_b) @ M
+        t = dense.reshape((chi_t,) * 6)
+        perm = list(coarse_order) + [3 + c for c in coarse_order]
+        want = np.transpose(t, perm)
+        got = O.ascend_case(h, u, w, case)
+        assert np.abs(got - want).max() < 1e-13, case
+        # descending: the 3 fine sites' reduced density of M rho M^T
+        rho = I.random_operator(rng, chi_t, symmetric=False)
+        inv = np.argsort(perm)
+        rho_nat = np.transpose(rho, inv).reshape(chi_t ** 3, chi_t ** 3)
+        fine = (M @ rho_nat @ M.T).reshape((chi_b,) * 12)
+        rest = [s for s in range(6) if s not in sites]
+        # partial trace over the other three fine sites
+        letters = "abcdefghijkl"
+        ket = list(letters[:6])
+        bra = list(letters[6:])
+        for s in rest:
+            bra[s] = ket[s]
+        spec = "".join(ket + bra) + "->" + "".join(ket[s] for s in sites) + "".join(bra[s] for s in sites)
+        want_d = np.einsum(spec, fine)
+        got_d = O.descend_case(rho, u, w, case)
+        assert np.abs(got_d - want_d).max() < 1e-13, case
+
+
+def test_ttn_special_case_identity_disentanglers():
+    """u = 1 turns the MERA layer into a binary-tree layer (Fig. 1a)."""
+    rng = _rng(6)
+    chi_b, chi_t = 2, 3
+    w = I.random_w(rng, chi_b, chi_t)
+    u = np.einsum("am,bn->abmn", np.eye(chi_b), np.eye(chi_b))
+    h = I.random_operator(rng, chi_b, symmetric=False)
+    wm = w.reshape(chi_b ** 2, chi_t)
+    w2 = np.kron(wm, wm)
+    x = w2.T @ np.kron(_mat(h), np.eye(chi_b)) @ w2
+    want_even = np.kron(np.eye(chi_t), x).reshape((chi_t,) * 6)
+    assert np.abs(O.ascend_case(h, u, w, "even") - want_even).max() < 1e-13
+    # odd position: h on the right leg under the first isometry and both
+    # legs under the second one; the third coarse site sees the identity
+    xo = w2.T @ np.kron(np.eye(chi_b), _mat(h)) @ w2
+    want_odd = np.kron(xo, np.eye(chi_t)).reshape((chi_t,) * 6)
+    assert np.abs(O.ascend_case(h, u, w, "odd") - want_odd).max() < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Environments are the energy gradient; the paper's contribution counts.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("chi_b,chi_t", [(2, 2), (3, 2), (2, 3)])
+def test_environments_are_half_the_gradient(chi_b, chi_t):
+    rng = _rng(7)
+    u, w = I.random_u(rng, chi_b), I.random_w(rng, chi_b, chi_t)
+    h = I.random_operator(rng, chi_b)
+    rho = I.random_operator(rng, chi_t)
+    gw = O.env_w(h, rho, u, w)
+    gu = O.env_u(h, rho, u, w)
+    eps = 1e-5
+    xw = rng.standard_normal(w.shape)
+    xu = rng.standard_normal(u.shape)
+    fd_w = (O.energy(h, rho, u, w + eps * xw) - O.energy(h, rho, u, w - eps * xw)) / (2 * eps)
+    fd_u = (O.energy(h, rho, u + eps * xu, w) - O.energy(h, rho, u - eps * xu, w)) / (2 * eps)
+    assert fd_w == pytest.approx(2 * np.sum(gw * xw), rel=1e-8, abs=1e-10)
+    assert fd_u == pytest.approx(2 * np.sum(gu * xu), rel=1e-8, abs=1e-10)
+
+
+def test_environment_contraction_closes_to_energy():
+    """Each hole, closed again with the removed tensor, gives E_case; so
+    <Gamma_w, w> = 3 E and <Gamma_u, u> = 2 E (6 and 4 terms, halved)."""
+    gold = json.load(open(GOLDEN))["env_contributions"]
+    rng = _rng(8)
+    chi = 2
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    h = I.random_operator(rng, chi)
+    rho = I.random_density(rng, chi)
+    e = O.energy(h, rho, u, w)
+    assert np.sum(O.env_w(h, rho, u, w) * w) == pytest.approx(gold["w"] / 2 * e, rel=1e-12)
+    assert np.sum(O.env_u(h, rho, u, w) * u) == pytest.approx(gold["u"] / 2 * e, rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Update (Fig. 5).
+# --------------------------------------------------------------------------
+def test_polar_update_closed_forms():
+    # env = R diag(3, 2): -U V^T = -R
+    th = 0.3
+    r = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    env = (r @ np.diag([3.0, 2.0])).reshape(2, 1, 2)
+    x = O.polar_update(env, 2).reshape(2, 2)
+    assert np.abs(x + r).max() < 1e-15
+    # rectangular: rows = lower legs, columns = upper leg
+    env = np.array([[2.0, 0.0], [0.0, 0.0], [0.0, 5.0], [0.0, 0.0]]).reshape(2, 2, 2)
+    x = O.polar_update(env, 2).reshape(4, 2)
+    want = -np.array([[1.0, 0.0], [0.0, 0.0], [0.0, 1.0], [0.0, 0.0]])
+    assert np.abs(x - want).max() < 1e-15
+
+
+@pytest.mark.parametrize("chi_b,chi_t", [(2, 2), (3, 2)])
+def test_update_fixed_by_minus_identity_hamiltonian(chi_b, chi_t):
+    """With h = -1 every isometric tensor is optimal: the update returns it."""
+    rng = _rng(9)
+    u, w = I.random_u(rng, chi_b), I.random_w(rng, chi_b, chi_t)
+    h = -np.eye(chi_b ** 3).reshape((chi_b,) * 6)
+    rho = I.random_density(rng, chi_t)
+    assert np.abs(O.update_u(h, rho, u, w) - u).max() < 1e-12
+    assert np.abs(O.update_w(h, rho, u, w) - w).max() < 1e-12
+
+
+def test_updates_satisfy_constraints():
+    rng = _rng(10)
+    chi_b, chi_t = 3, 2
+    u, w = I.random_u(rng, chi_b), I.random_w(rng, chi_b, chi_t)
+    h = I.random_operator(rng, chi_b)
+    rho = I.random_density(rng, chi_t)
+    un = O.update_u(h, rho, u, w).reshape(chi_b ** 2, chi_b ** 2)
+    wn = O.update_w(h, rho, u, w).reshape(chi_b ** 2, chi_t)
+    assert np.abs(un.T @ un - np.eye(chi_b ** 2)).max() < 1e-13   # Eq. (unitarity)
+    assert np.abs(wn.T @ wn - np.eye(chi_t)).max() < 1e-13       # Eq. (iso)
+
+
+# --------------------------------------------------------------------------
+# Fixed point and scaling dimensions.
+# --------------------------------------------------------------------------
+def test_fixed_point_is_a_fixed_point():
+    rng = _rng(11)
+    chi = 2
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    rho, resid = O.fixed_point_rho(u, w, O.identity_density(chi), 300)
+    assert resid < 1e-12
+    again = O.symmetrize_normalize(O.descend(rho, u, w))
+    assert np.abs(again - rho).max() < 1e-12
+    # dominant eigenvalue of D_SI is 1: the unnormalised map preserves the trace
+    assert np.trace(_mat(O.descend(rho, u, w))) == pytest.approx(1.0, abs=1e-14)
+
+
+def test_scaling_dimension_of_identity_is_zero():
+    gold = json.load(open(GOLDEN))["ising_cft_scaling_dims"]["value"]
+    rng = _rng(12)
+    u, w = I.random_u(rng, 2), I.random_w(rng, 2, 2)
+    dims = O.scaling_dimensions(u, w, 6)
+    assert dims[0] == pytest.approx(gold[0], abs=1e-12)
+    assert np.all(dims >= -1e-12)
+
+
+# --------------------------------------------------------------------------
+# Physics: the sweep lowers the energy towards -4/pi and stays above it.
+# --------------------------------------------------------------------------
+def test_sweeps_lower_energy_and_respect_variational_bound():
+    layers = I.init_mera(0, 4)
+    h1, shift = O.ising_h1(1.0)
+    layers, rho, es = O.run(layers, 1.0, n_sweeps=40, n_pow=20)
+    e_true = O.energy_per_spin(layers, h1, shift, rho, n_pow=200)
+    exact = O.exact_energy_per_spin(1.0)
+    assert e_true >= exact
+    assert es[-1] < es[0]
+    assert np.all(np.diff(es[5:]) < 1e-9)
+    assert (e_true - exact) / abs(exact) < 0.25
+    for u, w in layers:
+        um = u.reshape(u.shape[0] ** 2, -1)
+        wm = w.reshape(w.shape[0] ** 2, -1)
+        assert np.abs(um.T @ um - np.eye(um.shape[1])).max() < 1e-12
+        assert np.abs(wm.T @ wm - np.eye(wm.shape[1])).max() < 1e-12

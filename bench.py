@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark: optimisation sweeps of the scale-invariant binary MERA
+(critical transverse-field Ising chain, spins blocked in pairs, tau* = 3,
+20 power steps for rho* per sweep) on one GB300 per rank.
+
+A step is one full sweep (ascend h through the transitional layers, rho*
+power iteration, u/w environments and polar updates of every layer, rho
+descent, energy).  Inputs are synthetic (seeded QR isometries) and resident
+in HBM when the timed region starts; `e2e` repeats the measurement through
+the C ABI with host buffers (inputs copied in, energy copied out per step).
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead,
+on a bounded sample of the same workload (one diagram of the
+scale-invariant descending map per step), scaled to sweeps/s by flops.
+
+Multi-GPU: independent replicas (one MERA per rank, no data-path
+collective); the value is the sum of sweeps over ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MERA sweep iters/s & contraction TFLOP/s vs chi; mixed vs FP64 at dE<=1e-6/site"
+N_POW = 20
+HZ = 1.0
+SEED = 0
+# nominal dense tensor/FP64 rates (PFLOP/s) used only to carry the measured
+# BF16 peak over to the other dtypes
+NOMINAL = {"bf16": 2.25, "tf32": 1.1, "f64": 0.00125, "bf16x3": 2.25 / 3.0}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--chi", type=int, default=16)
+    ap.add_argument("--prec", default="f64", choices=["f64", "tf32", "bf16", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _peak_tflops(prec: str):
+    d, src = _peaks()
+    base = d.get("bf16_tflops_sustained", d.get("bf16_tflops"))
+    return base * NOMINAL[prec] / NOMINAL["bf16"], src
+
+
+def _sweep_flops(m, chi):
+    import mera_inputs as I
+
+    dims = I.layer_dims(chi)
+    total = 0.0
+    for k, (cb, ct) in enumerate(dims):
+        if k < len(dims) - 1:
+            total += m.mera_flops(m.OP_ASCEND, cb, ct)
+        else:
+            total += N_POW * m.mera_flops(m.OP_DESCEND, cb, ct)
+        total += m.mera_flops(m.OP_ENV_U, cb, ct) + m.mera_flops(m.OP_ENV_W, cb, ct)
+        if 0 < k < len(dims) - 1:
+            total += m.mera_flops(m.OP_DESCEND, cb, ct)
+        elif k == 0:
+            total += m.mera_flops(m.OP_ASCEND, cb, ct)
+    return total
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _cpu_baseline(chi: int, sweep_flops: float, diag_flops: float):
+    """Time one diagram of the SI descending map with the FP64 oracle."""
+    import numpy as np
+
+    import mera_inputs as I
+    from oracle import mera_oracle as O
+
+    rng = np.random.default_rng(SEED)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    rho = I.random_density(rng, chi)
+    t = time.perf_counter()
+    O.descend_case(rho, u, w, "even")
+    dt = time.perf_counter() - t
+    cores = int(os.environ.get("OMP_NUM_THREADS") or os.environ.get("OPENBLAS_NUM_THREADS") or os.cpu_count())
+    return {"value": (diag_flops / sweep_flops) / dt, "unit": "sweep/s", "cores": cores, "kind": "oracle",
+            "sample": f"one chi={chi} scale-invariant descending diagram (even position, {diag_flops:.3e} flop) "
+                      f"in {dt:.2f} s with numpy float64, scaled to a sweep ({sweep_flops:.3e} flop)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import paper_1906_12030_gb300 as m  # flop counts only (host planner, no device)
+
+    chi = args.chi
+    sweep_flops = _sweep_flops(m, chi)
+    diag_flops = m.mera_flops(m.OP_DESCEND, chi, chi) / 2
+    import numpy as np
+
+    import mera_inputs as I
+    from oracle import mera_oracle as O
+
+    rng = np.random.default_rng(SEED)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    rho = I.random_density(rng, chi)
+    for _ in range(args.warmup):
+        O.descend_case(rho, u, w, "even")
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        O.descend_case(rho, u, w, "even")
+        times.append(time.perf_counter() - t)
+    dt = sum(times) / len(times)
+    value = (diag_flops / sweep_flops) / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS") or os.environ.get("OPENBLAS_NUM_THREADS") or os.cpu_count())
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "sweep/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * sweep_flops / diag_flops * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "tflops": sweep_flops * value / 1e12,
+        "config": {"workload": f"critical-Ising scale-invariant binary MERA sweep, chi={chi}, tau*=3, "
+                               f"{N_POW} rho* power steps, blocked d=4", "chi": chi, "n_pow": N_POW, "hz": HZ,
+                   "prec": "f64"},
+        "cpu_baseline": {"value": value, "unit": "sweep/s", "cores": cores, "kind": "oracle",
+                         "sample": f"per step one chi={chi} SI descending diagram ({diag_flops:.3e} flop) with "
+                                   f"numpy float64, scaled to a sweep ({sweep_flops:.3e} flop)"},
+        "e2e": {"value": value, "unit": "sweep/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    import mera_inputs as I
+    import paper_1906_12030_gb300 as m
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    chi = args.chi
+    prec = m.PRECS[args.prec]
+    layers = I.init_mera(SEED, chi)
+    h1_host, shift = m.mera_ising_h1(HZ)
+    us = [torch.from_numpy(u).to(dev).reshape(-1).contiguous() for u, _ in layers]
+    ws_ = [torch.from_numpy(w).to(dev).contiguous() for _, w in layers]
+    n3 = chi ** 3
+    rho = (torch.eye(n3, dtype=torch.float64, device=dev) / n3).reshape(-1).contiguous()
+    h1 = torch.from_numpy(h1_host.reshape(-1)).to(dev)
+    state = m.MeraState(us, ws_, rho)
+    wsb = m.workspace(m.mera_sweep_workspace_size(state.chi_b, state.chi_t, prec), dev)
+    e = torch.empty(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def sweep():
+        try:
+            m.mera_sweep(state, h1, shift, N_POW, e, prec=prec, ws=wsb, stream=stream)
+        except m.MeraNotConverged:
+            pass  # a polar update hit its cap; the sweep is complete
+
+    for _ in range(args.warmup):
+        sweep()
+    torch.cuda.synchronize(dev)
+
+    sweep_flops = _sweep_flops(m, chi)
+    launches0 = m.mera_launch_count()
+    m.mera_profile_enable(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)  # evict L2 between timed steps (not timed)
+            starts[k].record(stream)
+            sweep()
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    launches = m.mera_launch_count() - launches0
+    step_ms = [s.elapsed_time(t) for s, t in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    dom = m.mera_profile_read(m.PROF_GEMM_DOMINANT)
+    allg = m.mera_profile_read(m.PROF_GEMM)
+    perm = m.mera_profile_read(m.PROF_PERMUTE)
+    m.mera_profile_enable(False)
+    energy = e.item()
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    e2e = None
+    if not args.no_e2e:
+        host = [t.detach().cpu().pin_memory() for t in us + ws_ + [rho, h1]]
+        devs = us + ws_ + [rho, h1]
+        e_host = torch.empty(1, dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host)
+        n_e2e = max(1, min(args.steps, 2))
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(n_e2e):
+            for hsrc, ddst in zip(host, devs):
+                ddst.copy_(hsrc, non_blocking=True)
+            sweep()
+            e_host.copy_(e, non_blocking=True)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = t.item()
+        e2e = {"value": world * n_e2e / (e2e_ms / 1e3), "unit": "sweep/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 8, "steps": n_e2e}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    value = world * args.steps / (total_ms / 1e3)
+    peak, peak_src = _peak_tflops(args.prec)
+    dom_tflops = dom[2] / (dom[1] / 1e3) / 1e12 if dom[1] > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "sweep/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+        "tflops": sweep_flops * value / 1e12,
+        "config": {"workload": f"critical-Ising scale-invariant binary MERA sweep, chi={chi}, tau*=3, "
+                               f"{N_POW} rho* power steps, blocked d=4", "chi": chi, "n_pow": N_POW, "hz": HZ,
+                   "prec": args.prec, "seed": SEED, "layer_dims": I.layer_dims(chi),
+                   "sweep_flops": sweep_flops, "parallelism": f"replicas{world}",
+                   "l2": "256 MB buffer written between timed steps (untimed); working set > L2"},
+        "energy_per_spin": energy,
+        "roofline": {"bound": "tensor" if args.prec != "f64" else "fp64", "achieved": dom_tflops, "peak": peak,
+                     "unit": "TFLOP/s", "frac": (dom_tflops / peak) if dom_tflops else None, "traffic": None,
+                     "kernel": "gemm_f64_kernel" if args.prec == "f64" else "tcgen05 GEMM",
+                     "launches": dom[0], "kernel_ms": dom[1], "peak_source": f"{peak_src} bf16 x nominal ratio"},
+        "stage_ms_per_step": {"gemm": allg[1] / args.steps, "gemm_dominant": dom[1] / args.steps,
+                              "permute": perm[1] / args.steps},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = _cpu_baseline(chi, sweep_flops, m.mera_flops(m.OP_DESCEND, chi, chi) / 2)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

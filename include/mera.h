@@ -1,0 +1,261 @@
+/*
+ * mera.h -- C ABI of the GB300 (sm_103a) library for the scale-invariant
+ * binary MERA of arXiv:1906.12030 ("TensorNetwork on TensorFlow:
+ * Entanglement Renormalization for quantum critical lattice models").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Real arithmetic in IEEE binary64 at the boundary.  The Ising Hamiltonian
+ *   (Eq. ham, Sec. II A) is real, so the complex conjugations of Eq. (iso)
+ *   and Eq. (unitarity) drop out.
+ * - Tensors are C-contiguous (row-major) with these leg orders:
+ *     w[a][b][c]        isometry, a,b lower (fine) legs of size chi_b,
+ *                       c upper (coarse) leg of size chi_t;   Eq. (iso)
+ *     u[a][b][m][n]     disentangler, a,b lower legs, m,n upper legs, all
+ *                       of size chi_b;                        Eq. (unitarity)
+ *     X[i1][i2][i3][j1][j2][j3]
+ *                       3-site operator (Hamiltonian density h or reduced
+ *                       density matrix rho): ket legs, then bra legs.
+ *   As matrices: w is (chi_b^2) x chi_t, u is (chi_b^2) x (chi_b^2), X is
+ *   (d^3) x (d^3).
+ * - Unless a parameter says "host", every tensor pointer is a DEVICE pointer
+ *   owned by the caller (for example allocated through PyTorch).  Inputs are
+ *   read-only.  Outputs must not alias inputs unless stated.
+ * - Every compute call is asynchronous on the given stream (NULL = the legacy
+ *   default stream).  Returned status codes report argument errors detected on
+ *   the host and launch errors; results are valid once the stream is
+ *   synchronised.
+ * - Scratch memory is the caller's: `ws` must hold at least the byte count
+ *   reported by mera_workspace_size for the same operation and sizes, and be
+ *   256-byte aligned.  The library allocates no device memory of its own.
+ * - prec selects the arithmetic of the contractions (the O(chi^9) part):
+ *     MERA_PREC_F64    binary64 everywhere (FP64 units),
+ *     MERA_PREC_TF32   tensor cores, TF32 operands, FP32 accumulation,
+ *     MERA_PREC_BF16   tensor cores, BF16 operands, FP32 accumulation,
+ *     MERA_PREC_BF16X3 tensor cores, each operand split into a BF16 pair
+ *                      (hi + lo), three products hi*hi + hi*lo + lo*hi,
+ *                      FP32 accumulation.
+ *   Polar updates, normalisation, traces and energies are binary64 always.
+ */
+#ifndef MERA_GB300_H
+#define MERA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int mera_status;
+#define MERA_OK 0
+#define MERA_EINVAL 1    /* bad size, pointer, alignment or mode            */
+#define MERA_ENOMEM 2    /* workspace smaller than mera_workspace_size      */
+#define MERA_ECUDA 3     /* CUDA launch / runtime error                     */
+#define MERA_ENOTCONV 4  /* iteration cap reached; output still written     */
+#define MERA_ETIMEOUT 5  /* a bounded device-side wait gave up              */
+
+#define MERA_PREC_F64 0
+#define MERA_PREC_TF32 1
+#define MERA_PREC_BF16 2
+#define MERA_PREC_BF16X3 3
+
+/* Operation ids for mera_workspace_size / mera_plan_json. */
+#define MERA_OP_ASCEND 0
+#define MERA_OP_DESCEND 1
+#define MERA_OP_ENV_U 2
+#define MERA_OP_ENV_W 3
+#define MERA_OP_ENERGY 4
+#define MERA_OP_FIXED_POINT 5
+
+/* Largest bond dimension accepted by any entry point. */
+#define MERA_MAX_CHI 64
+/* Most layers a mera_state may hold (tau* <= MERA_MAX_LAYERS). */
+#define MERA_MAX_LAYERS 8
+
+/* Library version string, e.g. "mera-gb300 0.1 sm_103a". */
+const char* mera_version(void);
+
+/* Text of the last error reported on the calling thread ("" if none). */
+const char* mera_last_error(void);
+
+/*
+ * Scratch bytes needed by one call of `op` (MERA_OP_*) with lower bond
+ * dimension chi_b, upper bond dimension chi_t and mode prec.  For
+ * MERA_OP_FIXED_POINT chi_b == chi_t == chi.  Writes the count to *bytes.
+ * Returns MERA_EINVAL for an unknown op/prec, chi outside [1, MERA_MAX_CHI],
+ * chi_t > chi_b^2, or a NULL `bytes`.
+ */
+mera_status mera_workspace_size(int op, int chi_b, int chi_t, int prec, size_t* bytes);
+
+/*
+ * Ascending superoperator (Fig. 4a, Sec. II B): h_out = A(h) =
+ * (A_even(h) + A_odd(h)) / 2, the 3-site operator h on the lattice below a
+ * layer (u, w) lifted to the lattice above it.  A_even places h on the right
+ * lower leg of one disentangler and both lower legs of the next; A_odd on
+ * both lower legs of one and the left lower leg of the next.
+ *   h      [chi_b^6]  input operator (any real operator, not only symmetric)
+ *   u      [chi_b^4]  disentangler of the layer
+ *   w      [chi_b^2 * chi_t] isometry of the layer
+ *   h_out  [chi_t^6]  output, overwritten; must not alias h
+ */
+mera_status mera_ascend(const double* h, const double* u, const double* w, int chi_b, int chi_t,
+                        double* h_out, int prec, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Descending superoperator (Fig. 4b, Sec. II B): rho_out = D(rho) =
+ * (D_even(rho) + D_odd(rho)) / 2, the Hilbert-Schmidt adjoint of A:
+ * <A(h), rho> = <h, D(rho)> with <X,Y> = sum_ij X_ij Y_ij.
+ *   rho     [chi_t^6]  3-site operator on the lattice above the layer
+ *   rho_out [chi_b^6]  output on the lattice below, overwritten
+ */
+mera_status mera_descend(const double* rho, const double* u, const double* w, int chi_b, int chi_t,
+                         double* rho_out, int prec, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Scale-invariant fixed point (Sec. II B: rho* is the dominant eigenvector of
+ * the scale-invariant descending superoperator, found by an iterative
+ * method).  Runs n_iter power steps  rho <- S(D(rho)) / tr S(D(rho)),  with
+ * S(X) = (X + X^T)/2 exchanging the ket and bra triples, in place.
+ *   u, w       SI-layer tensors with chi_b = chi_t = chi
+ *   rho_inout  [chi^6] start vector on entry (e.g. identity / chi^3, or the
+ *              previous sweep's rho*), the iterate on return
+ *   resid_dev  device double: ||rho_k - rho_{k-1}||_F of the last step
+ *              (0 if n_iter == 0); may be NULL
+ * Normalisation, symmetrisation and the residual are binary64 in every mode.
+ */
+mera_status mera_fixed_point_rho(const double* u, const double* w, int chi, double* rho_inout,
+                                 int n_iter, double* resid_dev, int prec, void* ws,
+                                 size_t ws_bytes, void* stream);
+
+/*
+ * Environment of the disentangler (Fig. 4d, Fig. A1b, Sec. II C): half the
+ * sum of the four networks of E = tr(A(h) rho) with one bra-side
+ * disentangler removed (two per causal-cone position).  For symmetric h and
+ * rho, dE/du = 2 * env.
+ *   h       [chi_b^6] operator below the layer;  rho [chi_t^6] above it
+ *   env_out [chi_b^4] output in u's leg order, overwritten
+ */
+mera_status mera_env_u(const double* h, const double* rho, const double* u, const double* w,
+                       int chi_b, int chi_t, double* env_out, int prec, void* ws, size_t ws_bytes,
+                       void* stream);
+
+/*
+ * Environment of the isometry (Fig. 4c, Fig. A1a): half the sum of the six
+ * networks of E with one bra-side isometry removed (three per position).
+ * dE/dw = 2 * env for symmetric h and rho.
+ *   env_out [chi_b^2 * chi_t] output in w's leg order, overwritten
+ */
+mera_status mera_env_w(const double* h, const double* rho, const double* u, const double* w,
+                       int chi_b, int chi_t, double* env_out, int prec, void* ws, size_t ws_bytes,
+                       void* stream);
+
+/*
+ * Update (Fig. 5, Sec. II C): out = -polar(env) = -U V^T where the m x n
+ * matrix env (row-major; rows = lower legs, columns = upper legs) has the
+ * thin SVD U S V^T.  Requires m >= n >= 1.  Binary64, computed on the device
+ * by the Newton-Schulz iteration X <- X (3 I - X^T X) / 2 from
+ * X0 = env / ||env||_F, which converges to the polar factor for full column
+ * rank.  Stops when ||X^T X - I||_F <= tol (tol <= 0 selects 1e-13 * sqrt(n))
+ * or after max_iter steps (<= 0 selects 100); in the latter case returns
+ * MERA_ENOTCONV with the last iterate written.  Synchronises the stream
+ * to test convergence.  out [m*n] must not alias env.
+ */
+mera_status mera_polar_update(const double* env, int m, int n, double* out, int max_iter,
+                              double tol, void* ws, size_t ws_bytes, void* stream);
+
+/* Scratch bytes for mera_polar_update with an m x n environment. */
+mera_status mera_polar_workspace_size(int m, int n, size_t* bytes);
+
+/*
+ * Energy term (Sec. II B): *e_dev = tr(A(h) rho) = sum A(h)[I][J] rho[J][I]
+ * with I, J the ket and bra triples.  e_dev is a device double.
+ */
+mera_status mera_energy(const double* h, const double* rho, const double* u, const double* w,
+                        int chi_b, int chi_t, double* e_dev, int prec, void* ws, size_t ws_bytes,
+                        void* stream);
+
+/*
+ * Blocked critical-Ising density (Eq. ham with spins blocked in pairs to a
+ * local dimension 4, Sec. II B 3-site regrouping): writes, to HOST memory,
+ * h1 = h3 - shift * 1 as a [4]^6 operator (4096 doubles) with
+ * shift = lambda_max(h3) so that h1 is negative semidefinite, and *shift.
+ * The field hz multiplies the Z terms; hz = 1 is the critical point.
+ */
+mera_status mera_ising_h1(double hz, double* h1_host, double* shift_host);
+
+/* One MERA: layers bottom first, the last one scale invariant (Sec. II A). */
+typedef struct {
+  int n_layers;                    /* tau*, 1..MERA_MAX_LAYERS              */
+  int chi_b[MERA_MAX_LAYERS];      /* lower bond dimension of each layer    */
+  int chi_t[MERA_MAX_LAYERS];      /* upper bond dimension of each layer    */
+  double* u[MERA_MAX_LAYERS];      /* device, chi_b^4, updated in place     */
+  double* w[MERA_MAX_LAYERS];      /* device, chi_b^2*chi_t, in place       */
+  double* rho_star;                /* device, chi_t[last]^6, warm start     */
+} mera_state;
+
+/*
+ * One optimisation sweep (Sec. II C): ascend h1 through the transitional
+ * layers, n_pow power steps for rho*, update the scale-invariant layer (u,
+ * then w with the new u) from its environment with h_{tau*} and rho*, then
+ * the transitional layers top-down (u, w, then descend rho one layer; the
+ * layer just below the scale-invariant ones sees rho* itself), and
+ * finally *e_dev = (tr(h1 rho1) + shift) / 2, the energy per spin with the
+ * new tensors.  Layer dimensions must chain: chi_t[k] == chi_b[k+1], and
+ * the last layer has chi_b == chi_t.  h1_dev is [chi_b[0]^6] on the device.
+ * Returns MERA_ENOTCONV if a polar update hit its iteration cap (the sweep
+ * is still completed).
+ */
+mera_status mera_sweep(mera_state* state, const double* h1_dev, double shift, int n_pow, int prec,
+                       void* ws, size_t ws_bytes, double* e_dev, void* stream);
+
+/* Scratch bytes for mera_sweep on a state with these dimensions. */
+mera_status mera_sweep_workspace_size(int n_layers, const int* chi_b, const int* chi_t, int prec,
+                                      size_t* bytes);
+
+/*
+ * Contraction program of `op` as JSON text (orders, GEMM shapes, layouts,
+ * flop counts) for inspection and host-side tests.  Writes at most `cap`
+ * bytes including the terminating NUL to `buf` and the full length
+ * (excluding NUL) to *len.  No device access.
+ */
+mera_status mera_plan_json(int op, int chi_b, int chi_t, int prec, char* buf, size_t cap,
+                           size_t* len);
+
+/*
+ * Algorithmic flop count of one call of `op` (the pairwise contraction
+ * program's GEMMs, 2 flops per multiply-add).  No device access.
+ */
+mera_status mera_flops(int op, int chi_b, int chi_t, double* flops);
+
+/* ------------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper; used to measure the kernels).
+ * ---------------------------------------------------------------------- */
+
+/* Number of CUDA kernels this library has launched since it was loaded. */
+long long mera_launch_count(void);
+
+/*
+ * Turn per-launch CUDA-event timing of the contraction kernels on (1) or off
+ * (0).  Both calls first wait for and discard earlier records.  While on,
+ * every GEMM and operand-permute launch is bracketed by two events recorded
+ * on its own stream.
+ */
+mera_status mera_profile_enable(int on);
+
+#define MERA_PROF_GEMM 0          /* every contraction GEMM                 */
+#define MERA_PROF_GEMM_DOMINANT 1 /* the chi^9-class GEMMs of each diagram  */
+#define MERA_PROF_PERMUTE 2       /* input permute/cast kernels             */
+
+/*
+ * Totals over the records since mera_profile_enable(1): launches, summed
+ * device milliseconds and summed algorithmic flops of the selected kind.
+ * Waits for the recorded events.  Any pointer may be NULL.
+ */
+mera_status mera_profile_read(int kind, long long* launches, double* ms, double* flops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MERA_GB300_H */

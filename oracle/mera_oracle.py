@@ -128,6 +128,23 @@ def ascend(h, u, w):
     return 0.5 * (ascend_case(h, u, w, "even") + ascend_case(h, u, w, "odd"))
 
 
+def ascend_rows(h, u, w, rows):
+    """Selected rows of A(h): for each ket triple (p, q, r) in `rows`, the
+    chi_t^3 entries A(h)[p, q, r, :, :, :].  The same networks as
+    ascend_case with the ket-side isometries' upper legs fixed, so a row
+    costs a factor chi_t less than the whole map (used to check full-size
+    results entry by entry)."""
+    out = []
+    for p, q, r in rows:
+        acc = 0.0
+        for case in ("even", "odd"):
+            ku, bu = _KET_U[case], _BRA_U[case]
+            spec = ",".join(["xa", "bc", "dy"] + ku + [_OP] + bu + _BRA_W) + "->stv"
+            acc = acc + _ein(spec, w[:, :, p], w[:, :, q], w[:, :, r], u, u, h, u, u, w, w, w)
+        out.append(0.5 * acc)
+    return np.stack(out)
+
+
 def descend_case(rho, u, w, case: str):
     """D_case(rho)[i,j,k,l,m,n]: the network of A_case with rho on the upper
     legs [p,q,r,s,t,v] and the lower legs open (Fig. 4b)."""
@@ -256,7 +273,8 @@ def sweep(layers, h1, shift, rho_star, n_pow: int = 20):
     2. rho* <- n_pow power iterations of the SI descending map (warm start),
     3. update the SI layer: u from its environment (h_{tau*}, rho*), then w
        with the new u,
-    4. transitional layers top-down: u, then w, then descend rho one layer,
+    4. transitional layers top-down: u, then w, then descend rho one layer
+       (the layer just below the SI layers sees rho* itself),
     5. energy per spin (tr(h1 rho1) + shift) / 2 with the new tensors.
     rho* is not recomputed between the SI update and the descent (reading).
     """
@@ -274,7 +292,9 @@ def sweep(layers, h1, shift, rho_star, n_pow: int = 20):
         u = update_u(hs[tau], rho_above, u, w)
         w = update_w(hs[tau], rho_above, u, w)
         layers[tau] = (u, w)
-        if tau > 0:
+        if 0 < tau < n - 1:
+            # rho_{tau*} = rho* sits on top of the last transitional layer;
+            # it is descended through the transitional layers only.
             rho_above = descend(rho_above, u, w)
     u1, w1 = layers[0]
     e_site = energy(h1, rho_above, u1, w1) + shift
@@ -299,7 +319,7 @@ def energy_per_spin(layers, h1, shift, rho0, n_pow: int = 200):
     then (tr(h1 rho1) + shift) / 2.  A variational upper bound on e0."""
     u, w = layers[-1]
     rho, _ = fixed_point_rho(u, w, rho0, n_pow)
-    for tau in range(len(layers) - 1, 0, -1):
+    for tau in range(len(layers) - 2, 0, -1):
         u, w = layers[tau]
         rho = descend(rho, u, w)
     u1, w1 = layers[0]

@@ -1,0 +1,320 @@
+"""ctypes binding of ``include/mera.h``: argument marshalling only.
+
+Each function has the name of its C entry point and forwards PyTorch
+tensors as raw device pointers.  Errors come back as :class:`MeraError`
+(carrying the C status and message); a missing library raises at import
+time of the first call, never falls back to another implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+import threading
+
+__all__ = [
+    "MeraError", "MeraNotConverged", "PREC_F64", "PREC_TF32", "PREC_BF16", "PREC_BF16X3", "PRECS",
+    "OP_ASCEND", "OP_DESCEND", "OP_ENV_U", "OP_ENV_W", "OP_ENERGY", "OP_FIXED_POINT",
+    "library", "library_path", "mera_version", "mera_workspace_size", "mera_ascend", "mera_descend",
+    "mera_fixed_point_rho", "mera_env_u", "mera_env_w", "mera_polar_update", "mera_polar_workspace_size",
+    "mera_energy", "mera_ising_h1", "mera_sweep", "mera_sweep_workspace_size", "mera_plan_json", "mera_flops",
+    "workspace", "MeraState", "mera_launch_count", "mera_profile_enable", "mera_profile_read",
+    "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE",
+]
+
+PREC_F64, PREC_TF32, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3
+PRECS = {"f64": PREC_F64, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x3": PREC_BF16X3}
+OP_ASCEND, OP_DESCEND, OP_ENV_U, OP_ENV_W, OP_ENERGY, OP_FIXED_POINT = 0, 1, 2, 3, 4, 5
+MAX_LAYERS = 8
+PROF_GEMM, PROF_GEMM_DOMINANT, PROF_PERMUTE = 0, 1, 2
+
+_OK, _EINVAL, _ENOMEM, _ECUDA, _ENOTCONV, _ETIMEOUT = 0, 1, 2, 3, 4, 5
+
+
+class MeraError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"mera status {status}: {message}")
+        self.status = status
+
+
+class MeraNotConverged(MeraError):
+    pass
+
+
+class _State(ctypes.Structure):
+    _fields_ = [
+        ("n_layers", ctypes.c_int),
+        ("chi_b", ctypes.c_int * MAX_LAYERS),
+        ("chi_t", ctypes.c_int * MAX_LAYERS),
+        ("u", ctypes.c_void_p * MAX_LAYERS),
+        ("w", ctypes.c_void_p * MAX_LAYERS),
+        ("rho_star", ctypes.c_void_p),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    from . import build as _build
+
+    return _build.LIB
+
+
+def library():
+    """Load (building in-tree if needed) the CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+
+        path = _build.LIB
+        if not os.path.exists(path):
+            path = _build.build()
+        lib = ctypes.CDLL(path)
+        vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        psz, pd = ctypes.POINTER(sz), ctypes.POINTER(d)
+        sig = {
+            "mera_version": ([], ctypes.c_char_p),
+            "mera_last_error": ([], ctypes.c_char_p),
+            "mera_workspace_size": ([i, i, i, i, psz], i),
+            "mera_ascend": ([vp, vp, vp, i, i, vp, i, vp, sz, vp], i),
+            "mera_descend": ([vp, vp, vp, i, i, vp, i, vp, sz, vp], i),
+            "mera_fixed_point_rho": ([vp, vp, i, vp, i, vp, i, vp, sz, vp], i),
+            "mera_env_u": ([vp, vp, vp, vp, i, i, vp, i, vp, sz, vp], i),
+            "mera_env_w": ([vp, vp, vp, vp, i, i, vp, i, vp, sz, vp], i),
+            "mera_polar_update": ([vp, i, i, vp, i, d, vp, sz, vp], i),
+            "mera_polar_workspace_size": ([i, i, psz], i),
+            "mera_energy": ([vp, vp, vp, vp, i, i, vp, i, vp, sz, vp], i),
+            "mera_ising_h1": ([d, vp, pd], i),
+            "mera_sweep": ([ctypes.POINTER(_State), vp, d, i, i, vp, sz, vp, vp], i),
+            "mera_sweep_workspace_size": ([i, ctypes.POINTER(i), ctypes.POINTER(i), i, psz], i),
+            "mera_plan_json": ([i, i, i, i, ctypes.c_char_p, sz, psz], i),
+            "mera_flops": ([i, i, i, pd], i),
+            "mera_launch_count": ([], ctypes.c_longlong),
+            "mera_profile_enable": ([i], i),
+            "mera_profile_read": ([i, ctypes.POINTER(ctypes.c_longlong), pd, pd], i),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(status: int):
+    if status == _OK:
+        return
+    msg = library().mera_last_error().decode(errors="replace")
+    if status == _ENOTCONV:
+        raise MeraNotConverged(status, msg)
+    raise MeraError(status, msg)
+
+
+def _dev(t, numel=None, name="tensor"):
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f64(t, numel, name):
+    import torch
+
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name} must be float64")
+    return _dev(t, numel, name)
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ws(ws):
+    if ws is None:
+        return ctypes.c_void_p(0), 0
+    return ctypes.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size()
+
+
+def mera_version() -> str:
+    return library().mera_version().decode()
+
+
+def mera_workspace_size(op: int, chi_b: int, chi_t: int, prec: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(library().mera_workspace_size(op, chi_b, chi_t, prec, ctypes.byref(n)))
+    return n.value
+
+
+def workspace(nbytes: int, device=None):
+    """A 256-byte aligned device scratch buffer of at least nbytes."""
+    import torch
+
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def _auto_ws(ws, op, chi_b, chi_t, prec, device):
+    if ws is not None:
+        return ws
+    return workspace(mera_workspace_size(op, chi_b, chi_t, prec), device)
+
+
+def mera_ascend(h, u, w, chi_b, chi_t, out, prec=PREC_F64, ws=None, stream=None):
+    ws = _auto_ws(ws, OP_ASCEND, chi_b, chi_t, prec, h.device)
+    p, n = _ws(ws)
+    _check(library().mera_ascend(_f64(h, chi_b ** 6, "h"), _f64(u, chi_b ** 4, "u"), _f64(w, chi_b ** 2 * chi_t, "w"),
+                                 chi_b, chi_t, _f64(out, chi_t ** 6, "out"), prec, p, n, _stream(stream)))
+    return out
+
+
+def mera_descend(rho, u, w, chi_b, chi_t, out, prec=PREC_F64, ws=None, stream=None):
+    ws = _auto_ws(ws, OP_DESCEND, chi_b, chi_t, prec, rho.device)
+    p, n = _ws(ws)
+    _check(library().mera_descend(_f64(rho, chi_t ** 6, "rho"), _f64(u, chi_b ** 4, "u"),
+                                  _f64(w, chi_b ** 2 * chi_t, "w"), chi_b, chi_t, _f64(out, chi_b ** 6, "out"), prec,
+                                  p, n, _stream(stream)))
+    return out
+
+
+def mera_fixed_point_rho(u, w, chi, rho_inout, n_iter, resid=None, prec=PREC_F64, ws=None, stream=None):
+    ws = _auto_ws(ws, OP_FIXED_POINT, chi, chi, prec, u.device)
+    p, n = _ws(ws)
+    _check(library().mera_fixed_point_rho(_f64(u, chi ** 4, "u"), _f64(w, chi ** 3, "w"), chi,
+                                          _f64(rho_inout, chi ** 6, "rho"), n_iter,
+                                          _f64(resid, 1, "resid") if resid is not None else None, prec, p, n,
+                                          _stream(stream)))
+    return rho_inout
+
+
+def mera_env_u(h, rho, u, w, chi_b, chi_t, out, prec=PREC_F64, ws=None, stream=None):
+    ws = _auto_ws(ws, OP_ENV_U, chi_b, chi_t, prec, h.device)
+    p, n = _ws(ws)
+    _check(library().mera_env_u(_f64(h, chi_b ** 6, "h"), _f64(rho, chi_t ** 6, "rho"), _f64(u, chi_b ** 4, "u"),
+                                _f64(w, chi_b ** 2 * chi_t, "w"), chi_b, chi_t, _f64(out, chi_b ** 4, "out"), prec, p,
+                                n, _stream(stream)))
+    return out
+
+
+def mera_env_w(h, rho, u, w, chi_b, chi_t, out, prec=PREC_F64, ws=None, stream=None):
+    ws = _auto_ws(ws, OP_ENV_W, chi_b, chi_t, prec, h.device)
+    p, n = _ws(ws)
+    _check(library().mera_env_w(_f64(h, chi_b ** 6, "h"), _f64(rho, chi_t ** 6, "rho"), _f64(u, chi_b ** 4, "u"),
+                                _f64(w, chi_b ** 2 * chi_t, "w"), chi_b, chi_t, _f64(out, chi_b ** 2 * chi_t, "out"),
+                                prec, p, n, _stream(stream)))
+    return out
+
+
+def mera_polar_workspace_size(m: int, n: int) -> int:
+    b = ctypes.c_size_t(0)
+    _check(library().mera_polar_workspace_size(m, n, ctypes.byref(b)))
+    return b.value
+
+
+def mera_polar_update(env, m, n, out, max_iter=0, tol=0.0, ws=None, stream=None):
+    if ws is None:
+        ws = workspace(mera_polar_workspace_size(m, n), env.device)
+    p, nb = _ws(ws)
+    _check(library().mera_polar_update(_f64(env, m * n, "env"), m, n, _f64(out, m * n, "out"), max_iter, tol, p, nb,
+                                       _stream(stream)))
+    return out
+
+
+def mera_energy(h, rho, u, w, chi_b, chi_t, e_out, prec=PREC_F64, ws=None, stream=None):
+    ws = _auto_ws(ws, OP_ENERGY, chi_b, chi_t, prec, h.device)
+    p, n = _ws(ws)
+    _check(library().mera_energy(_f64(h, chi_b ** 6, "h"), _f64(rho, chi_t ** 6, "rho"), _f64(u, chi_b ** 4, "u"),
+                                 _f64(w, chi_b ** 2 * chi_t, "w"), chi_b, chi_t, _f64(e_out, 1, "e_out"), prec, p, n,
+                                 _stream(stream)))
+    return e_out
+
+
+def mera_ising_h1(hz: float = 1.0):
+    """Host (numpy) [4]*6 shifted blocked Ising density and its shift."""
+    import numpy as np
+
+    h1 = np.zeros(4 ** 6, dtype=np.float64)
+    s = ctypes.c_double(0.0)
+    _check(library().mera_ising_h1(float(hz), h1.ctypes.data_as(ctypes.c_void_p), ctypes.byref(s)))
+    return h1.reshape((4,) * 6), s.value
+
+
+def mera_plan_json(op: int, chi_b: int, chi_t: int, prec: int = PREC_F64) -> dict:
+    lib = library()
+    n = ctypes.c_size_t(0)
+    _check(lib.mera_plan_json(op, chi_b, chi_t, prec, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check(lib.mera_plan_json(op, chi_b, chi_t, prec, buf, n.value + 1, ctypes.byref(n)))
+    return json.loads(buf.value.decode())
+
+
+def mera_flops(op: int, chi_b: int, chi_t: int) -> float:
+    f = ctypes.c_double(0.0)
+    _check(library().mera_flops(op, chi_b, chi_t, ctypes.byref(f)))
+    return f.value
+
+
+class MeraState:
+    """Device tensors of one MERA (layers bottom first) for :func:`mera_sweep`."""
+
+    def __init__(self, us, ws, rho_star):
+        self.us, self.ws, self.rho_star = list(us), list(ws), rho_star
+        self.chi_b = [int(round(w.shape[0])) for w in self.ws]
+        self.chi_t = [int(w.shape[2]) for w in self.ws]
+
+    def _c(self):
+        st = _State()
+        st.n_layers = len(self.us)
+        for k, (u, w) in enumerate(zip(self.us, self.ws)):
+            st.chi_b[k] = self.chi_b[k]
+            st.chi_t[k] = self.chi_t[k]
+            st.u[k] = _f64(u, self.chi_b[k] ** 4, "u").value
+            st.w[k] = _f64(w, self.chi_b[k] ** 2 * self.chi_t[k], "w").value
+        st.rho_star = _f64(self.rho_star, self.chi_t[-1] ** 6, "rho_star").value
+        return st
+
+
+def mera_sweep_workspace_size(chi_b, chi_t, prec) -> int:
+    n = len(chi_b)
+    cb = (ctypes.c_int * n)(*chi_b)
+    ct = (ctypes.c_int * n)(*chi_t)
+    b = ctypes.c_size_t(0)
+    _check(library().mera_sweep_workspace_size(n, cb, ct, prec, ctypes.byref(b)))
+    return b.value
+
+
+def mera_sweep(state: MeraState, h1, shift, n_pow, e_out, prec=PREC_F64, ws=None, stream=None):
+    if ws is None:
+        ws = workspace(mera_sweep_workspace_size(state.chi_b, state.chi_t, prec), h1.device)
+    p, n = _ws(ws)
+    st = state._c()
+    _check(library().mera_sweep(ctypes.byref(st), _f64(h1, state.chi_b[0] ** 6, "h1"), float(shift), n_pow, prec, p,
+                                n, _f64(e_out, 1, "e_out"), _stream(stream)))
+    return e_out
+
+
+def mera_launch_count() -> int:
+    return int(library().mera_launch_count())
+
+
+def mera_profile_enable(on: bool = True) -> None:
+    _check(library().mera_profile_enable(1 if on else 0))
+
+
+def mera_profile_read(kind: int = PROF_GEMM):
+    """(launches, device ms, algorithmic flops) since profiling was enabled."""
+    n, ms, fl = ctypes.c_longlong(0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(library().mera_profile_read(kind, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl)))
+    return n.value, ms.value, fl.value

@@ -1,0 +1,604 @@
+// C ABI of the MERA library: argument checks, contraction-program execution,
+// the scale-invariant fixed point, the polar update, the energy and the
+// native sweep driver.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "../../include/mera.h"
+#include "kernels.h"
+#include "plan.h"
+#include "tc_gemm.h"
+
+namespace mera {
+
+std::atomic<long long> g_launch_count{0};
+
+namespace {
+
+thread_local std::string g_err;
+
+// Optional CUDA-event timing of every GEMM / permute launch, recorded on the
+// launching stream.  Off by default; enabling it adds two event records per
+// launch and no synchronisation until the totals are read.
+struct Profiler {
+  std::mutex mu;
+  bool on = false;
+  struct Rec {
+    cudaEvent_t a, b;
+    int kind;  // 0 gemm, 1 permute
+    int dominant;
+    double flops;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void clear() {
+    for (auto& r : recs) {
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    recs.clear();
+  }
+};
+Profiler g_prof;
+
+struct ProfScope {
+  cudaStream_t s;
+  bool on;
+  Profiler::Rec rec{};
+  ProfScope(cudaStream_t st, int kind, int dominant, double flops) : s(st) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    on = g_prof.on;
+    if (!on) return;
+    rec.a = g_prof.get();
+    rec.b = g_prof.get();
+    rec.kind = kind;
+    rec.dominant = dominant;
+    rec.flops = flops;
+    cudaEventRecord(rec.a, s);
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(rec.b, s);
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.recs.push_back(rec);
+  }
+};
+
+mera_status fail(mera_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+mera_status cuda_status(cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return MERA_OK;
+  return fail(MERA_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+constexpr size_t kAlign = 256;
+constexpr size_t align_up_const(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+size_t align_up(size_t x) { return align_up_const(x); }
+
+bool chi_ok(int chi_b, int chi_t) {
+  return chi_b >= 1 && chi_t >= 1 && chi_b <= MERA_MAX_CHI && chi_t <= MERA_MAX_CHI &&
+         int64_t(chi_t) <= int64_t(chi_b) * chi_b;
+}
+bool prec_ok(int prec) { return prec >= MERA_PREC_F64 && prec <= MERA_PREC_BF16X3; }
+
+int64_t ipow(int64_t b, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+// Small scratch that reductions need (partials + scalars), bytes.
+constexpr size_t kReduceBytes = align_up_const(size_t(4096 + 8) * sizeof(double));
+
+// Bump allocator over the caller's workspace.
+struct Arena {
+  char* base;
+  size_t cap, used = 0;
+  char* take(size_t bytes) {
+    char* p = base + used;
+    used += align_up(bytes);
+    return p;
+  }
+};
+
+// Execute a contraction program; inputs[slot] are device pointers.
+mera_status run_program(const OpProgram& prog, const double* const inputs[4], double* out, int prec, char* ws,
+                        cudaStream_t stream) {
+  for (const Program& dg : prog.diagrams) {
+    for (const Step& st : dg.steps) {
+      if (st.kind == 0) {
+        const PermuteStep& p = st.p;
+        const Buffer& b = dg.bufs[p.dst_buf];
+        const int64_t plane = b.plane_bytes / elem_bytes(prec);
+        ProfScope ps(stream, 1, 0, 0.0);
+        cudaError_t e = launch_permute(p, inputs[p.slot], ws + b.offset, plane, prec, stream);
+        if (e != cudaSuccess) return cuda_status(e, "permute");
+        continue;
+      }
+      const GemmStep& g = st.g;
+      const Buffer& a = dg.bufs[g.a_buf];
+      const Buffer& b = dg.bufs[g.b_buf];
+      ProfScope ps(stream, 0, g.dominant, g.flops);
+      if (prec == PREC_F64) {
+        GemmF64Args args;
+        args.A = reinterpret_cast<const double*>(ws + a.offset);
+        args.a_m = g.lda;
+        args.a_k = 1;
+        args.B = reinterpret_cast<const double*>(ws + b.offset);
+        args.b_n = g.ldb;
+        args.b_k = 1;
+        args.M = g.M;
+        args.N = g.N;
+        args.K = g.K;
+        args.C = g.c_buf >= 0 ? reinterpret_cast<double*>(ws + dg.bufs[g.c_buf].offset) : out;
+        args.m_dst = g.m_dst;
+        args.n_dst = g.n_dst;
+        args.alpha = g.alpha;
+        args.accumulate = g.accumulate;
+        cudaError_t e = launch_gemm_f64(args, stream);
+        if (e != cudaSuccess) return cuda_status(e, "gemm_f64");
+      } else {
+        TcGemmArgs args;
+        args.prec = prec;
+        args.A = ws + a.offset;
+        args.a_plane_bytes = a.plane_bytes;
+        args.lda = g.lda;
+        args.B = ws + b.offset;
+        args.b_plane_bytes = b.plane_bytes;
+        args.ldb = g.ldb;
+        args.M = g.M;
+        args.N = g.N;
+        args.K = g.K;
+        args.c_final = g.c_buf < 0;
+        args.C = g.c_buf >= 0 ? static_cast<void*>(ws + dg.bufs[g.c_buf].offset) : static_cast<void*>(out);
+        args.c_plane_elems = g.c_buf >= 0 ? dg.bufs[g.c_buf].plane_bytes / elem_bytes(prec) : 0;
+        args.m_dst = g.m_dst;
+        args.n_dst = g.n_dst;
+        args.alpha = g.alpha;
+        args.accumulate = g.accumulate;
+        cudaError_t e = launch_gemm_tc(args, stream);
+        if (e == cudaErrorNotSupported) return fail(MERA_EINVAL, "tensor-core GEMM unavailable for prec %d", prec);
+        if (e != cudaSuccess) return cuda_status(e, "gemm_tc");
+      }
+    }
+  }
+  return MERA_OK;
+}
+
+// Workspace bytes of each composite operation.
+size_t op_bytes(const OpProgram& p) { return align_up(p.ws_bytes); }
+
+mera_status map_call(int op, const double* h, const double* rho, const double* u, const double* w, int chi_b,
+                     int chi_t, double* out, int prec, void* ws, size_t ws_bytes, void* stream) {
+  if (!chi_ok(chi_b, chi_t)) return fail(MERA_EINVAL, "bad bond dimensions chi_b=%d chi_t=%d", chi_b, chi_t);
+  if (!prec_ok(prec)) return fail(MERA_EINVAL, "bad prec %d", prec);
+  if (!u || !w || !out) return fail(MERA_EINVAL, "null tensor pointer");
+  if ((op == OP_ASCEND || op == OP_ENV_U || op == OP_ENV_W) && !h) return fail(MERA_EINVAL, "null h");
+  if ((op == OP_DESCEND || op == OP_ENV_U || op == OP_ENV_W) && !rho) return fail(MERA_EINVAL, "null rho");
+  const OpProgram* prog = get_program(op, chi_b, chi_t, prec);
+  if (!prog) return fail(MERA_EINVAL, "no contraction program");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(MERA_EINVAL, "workspace not 256-byte aligned");
+  if (ws_bytes < op_bytes(*prog) || (!ws && op_bytes(*prog) > 0))
+    return fail(MERA_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, op_bytes(*prog));
+  const double* inputs[4] = {h, rho, u, w};
+  return run_program(*prog, inputs, out, prec, static_cast<char*>(ws), static_cast<cudaStream_t>(stream));
+}
+
+}  // namespace
+}  // namespace mera
+
+using namespace mera;
+
+// ---------------------------------------------------------------------------
+extern "C" const char* mera_version(void) { return "mera-gb300 0.1 sm_103a"; }
+extern "C" const char* mera_last_error(void) { return g_err.c_str(); }
+
+static mera_status ws_size_impl(int op, int chi_b, int chi_t, int prec, size_t* bytes) {
+  if (!bytes) return fail(MERA_EINVAL, "null bytes");
+  if (!chi_ok(chi_b, chi_t) || !prec_ok(prec)) return fail(MERA_EINVAL, "bad sizes or prec");
+  switch (op) {
+    case MERA_OP_ASCEND:
+    case MERA_OP_DESCEND:
+    case MERA_OP_ENV_U:
+    case MERA_OP_ENV_W: {
+      const OpProgram* p = get_program(op, chi_b, chi_t, prec);
+      if (!p) return fail(MERA_EINVAL, "no contraction program");
+      *bytes = op_bytes(*p);
+      return MERA_OK;
+    }
+    case MERA_OP_ENERGY: {
+      const OpProgram* p = get_program(OP_ASCEND, chi_b, chi_t, prec);
+      if (!p) return fail(MERA_EINVAL, "no contraction program");
+      *bytes = op_bytes(*p) + align_up(ipow(chi_t, 6) * sizeof(double)) + kReduceBytes;
+      return MERA_OK;
+    }
+    case MERA_OP_FIXED_POINT: {
+      if (chi_b != chi_t) return fail(MERA_EINVAL, "fixed point needs chi_b == chi_t");
+      const OpProgram* p = get_program(OP_DESCEND, chi_b, chi_t, prec);
+      if (!p) return fail(MERA_EINVAL, "no contraction program");
+      *bytes = op_bytes(*p) + align_up(ipow(chi_t, 6) * sizeof(double)) + kReduceBytes;
+      return MERA_OK;
+    }
+    default:
+      return fail(MERA_EINVAL, "unknown op %d", op);
+  }
+}
+
+extern "C" mera_status mera_workspace_size(int op, int chi_b, int chi_t, int prec, size_t* bytes) {
+  return ws_size_impl(op, chi_b, chi_t, prec, bytes);
+}
+
+extern "C" mera_status mera_ascend(const double* h, const double* u, const double* w, int chi_b, int chi_t,
+                                   double* h_out, int prec, void* ws, size_t ws_bytes, void* stream) {
+  if (h_out && h_out == h) return fail(MERA_EINVAL, "h_out aliases h");
+  return map_call(OP_ASCEND, h, nullptr, u, w, chi_b, chi_t, h_out, prec, ws, ws_bytes, stream);
+}
+
+extern "C" mera_status mera_descend(const double* rho, const double* u, const double* w, int chi_b, int chi_t,
+                                    double* rho_out, int prec, void* ws, size_t ws_bytes, void* stream) {
+  if (rho_out && rho_out == rho) return fail(MERA_EINVAL, "rho_out aliases rho");
+  return map_call(OP_DESCEND, nullptr, rho, u, w, chi_b, chi_t, rho_out, prec, ws, ws_bytes, stream);
+}
+
+extern "C" mera_status mera_env_u(const double* h, const double* rho, const double* u, const double* w, int chi_b,
+                                  int chi_t, double* env_out, int prec, void* ws, size_t ws_bytes, void* stream) {
+  return map_call(OP_ENV_U, h, rho, u, w, chi_b, chi_t, env_out, prec, ws, ws_bytes, stream);
+}
+
+extern "C" mera_status mera_env_w(const double* h, const double* rho, const double* u, const double* w, int chi_b,
+                                  int chi_t, double* env_out, int prec, void* ws, size_t ws_bytes, void* stream) {
+  return map_call(OP_ENV_W, h, rho, u, w, chi_b, chi_t, env_out, prec, ws, ws_bytes, stream);
+}
+
+extern "C" mera_status mera_energy(const double* h, const double* rho, const double* u, const double* w, int chi_b,
+                                   int chi_t, double* e_dev, int prec, void* ws, size_t ws_bytes, void* stream) {
+  size_t need = 0;
+  mera_status st = ws_size_impl(MERA_OP_ENERGY, chi_b, chi_t, prec, &need);
+  if (st != MERA_OK) return st;
+  if (!h || !rho || !u || !w || !e_dev) return fail(MERA_EINVAL, "null pointer");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(MERA_EINVAL, "workspace not 256-byte aligned");
+  if (!ws || ws_bytes < need) return fail(MERA_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+  const OpProgram* prog = get_program(OP_ASCEND, chi_b, chi_t, prec);
+  Arena ar{static_cast<char*>(ws), ws_bytes};
+  char* pws = ar.take(op_bytes(*prog));
+  const int64_t n = ipow(chi_t, 3);
+  double* a = reinterpret_cast<double*>(ar.take(n * n * sizeof(double)));
+  double* partials = reinterpret_cast<double*>(ar.take(kReduceBytes));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double* inputs[4] = {h, nullptr, u, w};
+  st = run_program(*prog, inputs, a, prec, pws, s);
+  if (st != MERA_OK) return st;
+  return cuda_status(launch_dot_transposed(a, rho, n, partials, e_dev, s), "energy dot");
+}
+
+extern "C" mera_status mera_fixed_point_rho(const double* u, const double* w, int chi, double* rho_inout, int n_iter,
+                                            double* resid_dev, int prec, void* ws, size_t ws_bytes, void* stream) {
+  size_t need = 0;
+  mera_status st = ws_size_impl(MERA_OP_FIXED_POINT, chi, chi, prec, &need);
+  if (st != MERA_OK) return st;
+  if (!u || !w || !rho_inout) return fail(MERA_EINVAL, "null pointer");
+  if (n_iter < 0) return fail(MERA_EINVAL, "negative n_iter");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(MERA_EINVAL, "workspace not 256-byte aligned");
+  if (!ws || ws_bytes < need) return fail(MERA_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n_iter == 0) {
+    if (resid_dev) return cuda_status(cudaMemsetAsync(resid_dev, 0, sizeof(double), s), "memset");
+    return MERA_OK;
+  }
+  const OpProgram* prog = get_program(OP_DESCEND, chi, chi, prec);
+  Arena ar{static_cast<char*>(ws), ws_bytes};
+  char* pws = ar.take(op_bytes(*prog));
+  const int64_t n = ipow(chi, 3);
+  double* tmp = reinterpret_cast<double*>(ar.take(n * n * sizeof(double)));
+  double* red = reinterpret_cast<double*>(ar.take(kReduceBytes));
+  double* scalars = red + 4096;
+  const double* inputs[4] = {nullptr, rho_inout, u, w};
+  for (int it = 0; it < n_iter; ++it) {
+    st = run_program(*prog, inputs, tmp, prec, pws, s);
+    if (st != MERA_OK) return st;
+    cudaError_t e = launch_sym_normalize(tmp, rho_inout, n, red, scalars, resid_dev, s);
+    if (e != cudaSuccess) return cuda_status(e, "sym_normalize");
+  }
+  return MERA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Polar update.
+// ---------------------------------------------------------------------------
+static size_t polar_bytes(int m, int n) {
+  return 2 * align_up(size_t(m) * n * sizeof(double)) + 2 * align_up(size_t(n) * n * sizeof(double)) +
+         kReduceBytes;
+}
+
+extern "C" mera_status mera_polar_workspace_size(int m, int n, size_t* bytes) {
+  if (!bytes || m < 1 || n < 1 || m < n || m > 1 << 16) return fail(MERA_EINVAL, "bad polar sizes");
+  *bytes = polar_bytes(m, n);
+  return MERA_OK;
+}
+
+extern "C" mera_status mera_polar_update(const double* env, int m, int n, double* out, int max_iter, double tol,
+                                         void* ws, size_t ws_bytes, void* stream) {
+  if (!env || !out || env == out) return fail(MERA_EINVAL, "bad env/out pointers");
+  if (m < 1 || n < 1 || m < n || m > 1 << 16) return fail(MERA_EINVAL, "polar needs m >= n >= 1 (m=%d n=%d)", m, n);
+  const size_t need = polar_bytes(m, n);
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(MERA_EINVAL, "workspace not 256-byte aligned");
+  if (!ws || ws_bytes < need) return fail(MERA_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+  if (max_iter <= 0) max_iter = 100;
+  if (!(tol > 0)) tol = 1e-13 * std::sqrt(double(n));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Arena ar{static_cast<char*>(ws), ws_bytes};
+  double* X = reinterpret_cast<double*>(ar.take(size_t(m) * n * sizeof(double)));
+  double* Xn = reinterpret_cast<double*>(ar.take(size_t(m) * n * sizeof(double)));
+  double* G = reinterpret_cast<double*>(ar.take(size_t(n) * n * sizeof(double)));
+  double* Bm = reinterpret_cast<double*>(ar.take(size_t(n) * n * sizeof(double)));
+  double* red = reinterpret_cast<double*>(ar.take(kReduceBytes));
+  double* scalars = red + 4096;
+  cudaError_t e = launch_frob_scale(env, X, int64_t(m) * n, red, scalars, s);
+  if (e != cudaSuccess) return cuda_status(e, "polar init");
+  LegMap row_n, col_1, row_m;  // G / Bm (n x n) and X (m x n) destinations
+  row_n.n = 1; row_n.dim[0] = n; row_n.stride[0] = n;
+  col_1.n = 1; col_1.dim[0] = n; col_1.stride[0] = 1;
+  row_m.n = 1; row_m.dim[0] = m; row_m.stride[0] = n;
+  bool converged = false;
+  double resid = 0.0;
+  for (int it = 0; it < max_iter; ++it) {
+    // G = X^T X
+    GemmF64Args g;
+    g.A = X; g.a_m = 1; g.a_k = n;
+    g.B = X; g.b_n = 1; g.b_k = n;
+    g.M = n; g.N = n; g.K = m;
+    g.C = G; g.m_dst = row_n; g.n_dst = col_1; g.alpha = 1.0; g.accumulate = 0;
+    if ((e = launch_gemm_f64(g, s)) != cudaSuccess) return cuda_status(e, "polar gemm 1");
+    if ((e = launch_ns_combine(G, Bm, n, red, scalars + 1, s)) != cudaSuccess) return cuda_status(e, "polar combine");
+    // Xn = X Bm
+    g.A = X; g.a_m = n; g.a_k = 1;
+    g.B = Bm; g.b_n = 1; g.b_k = n;
+    g.M = m; g.N = n; g.K = n;
+    g.C = Xn; g.m_dst = row_m; g.n_dst = col_1;
+    if ((e = launch_gemm_f64(g, s)) != cudaSuccess) return cuda_status(e, "polar gemm 2");
+    std::swap(X, Xn);
+    if ((e = cudaMemcpyAsync(&resid, scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return cuda_status(e, "polar residual copy");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e, "polar sync");
+    if (!std::isfinite(resid)) break;
+    if (resid <= tol) {
+      converged = true;
+      break;
+    }
+  }
+  e = launch_scale_copy(X, out, int64_t(m) * n, -1.0, s);
+  if (e != cudaSuccess) return cuda_status(e, "polar output");
+  if (!converged) return fail(MERA_ENOTCONV, "polar iteration did not converge (resid %.3e, tol %.3e)", resid, tol);
+  return MERA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sweep.
+// ---------------------------------------------------------------------------
+namespace mera {
+namespace sweep_detail {
+
+struct SweepLayout {
+  size_t h_off[MERA_MAX_LAYERS];  // ascended Hamiltonians (layer >= 1)
+  size_t rho_off[2];              // ping-pong descended densities
+  size_t env_off, etmp_off, red_off, map_off, total;
+  size_t map_bytes;
+};
+
+mera_status sweep_layout(int n_layers, const int* chi_b, const int* chi_t, int prec, SweepLayout* L) {
+  if (n_layers < 1 || n_layers > MERA_MAX_LAYERS) return fail(MERA_EINVAL, "bad n_layers %d", n_layers);
+  for (int t = 0; t < n_layers; ++t) {
+    if (!chi_ok(chi_b[t], chi_t[t])) return fail(MERA_EINVAL, "bad dims in layer %d", t);
+    if (t + 1 < n_layers && chi_t[t] != chi_b[t + 1]) return fail(MERA_EINVAL, "layer dims do not chain at %d", t);
+  }
+  if (chi_b[n_layers - 1] != chi_t[n_layers - 1]) return fail(MERA_EINVAL, "scale-invariant layer needs chi_b == chi_t");
+  if (!prec_ok(prec)) return fail(MERA_EINVAL, "bad prec");
+  size_t off = 0, map_bytes = 0, rho_max = 0, env_max = 0;
+  for (int t = 0; t < n_layers; ++t) {
+    L->h_off[t] = off;
+    if (t >= 1) off += align_up(size_t(ipow(chi_b[t], 6)) * sizeof(double));
+    rho_max = std::max(rho_max, size_t(ipow(chi_b[t], 6)));
+    env_max = std::max(env_max, size_t(ipow(chi_b[t], 4)));
+    for (int op : {OP_ASCEND, OP_DESCEND, OP_ENV_U, OP_ENV_W}) {
+      const OpProgram* p = get_program(op, chi_b[t], chi_t[t], prec);
+      if (!p) return fail(MERA_EINVAL, "no program for layer %d", t);
+      map_bytes = std::max(map_bytes, op_bytes(*p));
+    }
+    const int64_t eb = int64_t(chi_b[t]) * chi_b[t];
+    map_bytes = std::max(map_bytes, polar_bytes(int(eb), int(eb)));
+    size_t fp = 0;
+    if (t == n_layers - 1) {
+      ws_size_impl(MERA_OP_FIXED_POINT, chi_b[t], chi_t[t], prec, &fp);
+      map_bytes = std::max(map_bytes, fp);
+    }
+    if (t == 0) {
+      ws_size_impl(MERA_OP_ENERGY, chi_b[t], chi_t[t], prec, &fp);
+      map_bytes = std::max(map_bytes, fp);
+    }
+  }
+  L->rho_off[0] = off;
+  off += align_up(rho_max * sizeof(double));
+  L->rho_off[1] = off;
+  off += align_up(rho_max * sizeof(double));
+  L->env_off = off;
+  off += align_up(env_max * sizeof(double));
+  L->etmp_off = off;
+  off += align_up(sizeof(double) * 2);
+  L->red_off = off;
+  off += kReduceBytes;
+  L->map_off = off;
+  L->map_bytes = map_bytes;
+  off += map_bytes;
+  L->total = off;
+  return MERA_OK;
+}
+
+__global__ void energy_per_spin_kernel(const double* tr, double shift, double* e) { *e = 0.5 * (*tr + shift); }
+
+}  // namespace sweep_detail
+}  // namespace mera
+
+using namespace mera::sweep_detail;
+
+extern "C" mera_status mera_sweep_workspace_size(int n_layers, const int* chi_b, const int* chi_t, int prec,
+                                                 size_t* bytes) {
+  if (!chi_b || !chi_t || !bytes) return fail(MERA_EINVAL, "null argument");
+  SweepLayout L;
+  mera_status st = sweep_layout(n_layers, chi_b, chi_t, prec, &L);
+  if (st != MERA_OK) return st;
+  *bytes = L.total;
+  return MERA_OK;
+}
+
+extern "C" mera_status mera_sweep(mera_state* S, const double* h1, double shift, int n_pow, int prec, void* ws,
+                                  size_t ws_bytes, double* e_dev, void* stream) {
+  if (!S || !h1 || !e_dev) return fail(MERA_EINVAL, "null argument");
+  const int n = S->n_layers;
+  SweepLayout L;
+  mera_status st = sweep_layout(n, S->chi_b, S->chi_t, prec, &L);
+  if (st != MERA_OK) return st;
+  for (int t = 0; t < n; ++t)
+    if (!S->u[t] || !S->w[t]) return fail(MERA_EINVAL, "null tensor in layer %d", t);
+  if (!S->rho_star) return fail(MERA_EINVAL, "null rho_star");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(MERA_EINVAL, "workspace not 256-byte aligned");
+  if (!ws || ws_bytes < L.total) return fail(MERA_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, L.total);
+  char* base = static_cast<char*>(ws);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double* hs[MERA_MAX_LAYERS];
+  hs[0] = h1;
+  for (int t = 1; t < n; ++t) hs[t] = reinterpret_cast<double*>(base + L.h_off[t]);
+  void* mws = base + L.map_off;
+  const size_t mb = L.map_bytes;
+  // 1. ascend the Hamiltonian density through the transitional layers
+  for (int t = 0; t + 1 < n; ++t) {
+    st = mera_ascend(hs[t], S->u[t], S->w[t], S->chi_b[t], S->chi_t[t], const_cast<double*>(hs[t + 1]), prec, mws,
+                     mb, stream);
+    if (st != MERA_OK) return st;
+  }
+  // 2. scale-invariant fixed point (warm start from the state's rho*)
+  st = mera_fixed_point_rho(S->u[n - 1], S->w[n - 1], S->chi_t[n - 1], S->rho_star, n_pow, nullptr, prec, mws, mb,
+                            stream);
+  if (st != MERA_OK) return st;
+  // 3./4. updates, scale-invariant layer first, then top-down
+  double* env = reinterpret_cast<double*>(base + L.env_off);
+  const double* rho_above = S->rho_star;
+  int ping = 0;
+  bool notconv = false;
+  for (int t = n - 1; t >= 0; --t) {
+    const int cb = S->chi_b[t], ct = S->chi_t[t];
+    st = mera_env_u(hs[t], rho_above, S->u[t], S->w[t], cb, ct, env, prec, mws, mb, stream);
+    if (st != MERA_OK) return st;
+    st = mera_polar_update(env, cb * cb, cb * cb, S->u[t], 0, 0.0, mws, mb, stream);
+    if (st == MERA_ENOTCONV) notconv = true;
+    else if (st != MERA_OK) return st;
+    st = mera_env_w(hs[t], rho_above, S->u[t], S->w[t], cb, ct, env, prec, mws, mb, stream);
+    if (st != MERA_OK) return st;
+    st = mera_polar_update(env, cb * cb, ct, S->w[t], 0, 0.0, mws, mb, stream);
+    if (st == MERA_ENOTCONV) notconv = true;
+    else if (st != MERA_OK) return st;
+    if (t > 0 && t < n - 1) {  // rho* sits on top of the last transitional layer
+      double* dst = reinterpret_cast<double*>(base + L.rho_off[ping]);
+      ping ^= 1;
+      st = mera_descend(rho_above, S->u[t], S->w[t], cb, ct, dst, prec, mws, mb, stream);
+      if (st != MERA_OK) return st;
+      rho_above = dst;
+    }
+  }
+  // 5. energy per spin with the new tensors
+  double* etmp = reinterpret_cast<double*>(base + L.etmp_off);
+  st = mera_energy(h1, rho_above, S->u[0], S->w[0], S->chi_b[0], S->chi_t[0], etmp, prec, mws, mb, stream);
+  if (st != MERA_OK) return st;
+  energy_per_spin_kernel<<<1, 1, 0, s>>>(etmp, shift, e_dev);
+  st = cuda_status(cudaGetLastError(), "energy per spin");
+  if (st != MERA_OK) return st;
+  if (notconv) return fail(MERA_ENOTCONV, "a polar update hit its iteration cap");
+  return MERA_OK;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" mera_status mera_plan_json(int op, int chi_b, int chi_t, int prec, char* buf, size_t cap, size_t* len) {
+  if (!chi_ok(chi_b, chi_t) || !prec_ok(prec) || op < 0 || op > 3) return fail(MERA_EINVAL, "bad arguments");
+  const OpProgram* p = get_program(op, chi_b, chi_t, prec);
+  if (!p) return fail(MERA_EINVAL, "no contraction program");
+  const std::string js = program_json(*p, op, chi_b, chi_t, prec);
+  if (len) *len = js.size();
+  if (buf && cap > 0) {
+    const size_t k = std::min(cap - 1, js.size());
+    std::memcpy(buf, js.data(), k);
+    buf[k] = '\0';
+  }
+  return MERA_OK;
+}
+
+extern "C" mera_status mera_flops(int op, int chi_b, int chi_t, double* flops) {
+  if (!flops || !chi_ok(chi_b, chi_t)) return fail(MERA_EINVAL, "bad arguments");
+  int base_op = op;
+  if (op == MERA_OP_ENERGY) base_op = OP_ASCEND;
+  if (op == MERA_OP_FIXED_POINT) base_op = OP_DESCEND;
+  if (base_op < 0 || base_op > 3) return fail(MERA_EINVAL, "bad op");
+  const OpProgram* p = get_program(base_op, chi_b, chi_t, MERA_PREC_F64);
+  if (!p) return fail(MERA_EINVAL, "no contraction program");
+  *flops = p->flops;
+  return MERA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Instrumentation.
+// ---------------------------------------------------------------------------
+extern "C" long long mera_launch_count(void) { return g_launch_count.load(); }
+
+extern "C" mera_status mera_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  for (auto& r : g_prof.recs) cudaEventSynchronize(r.b);
+  g_prof.clear();
+  g_prof.on = on != 0;
+  return MERA_OK;
+}
+
+extern "C" mera_status mera_profile_read(int kind, long long* launches, double* ms, double* flops) {
+  if (kind < 0 || kind > 2) return fail(MERA_EINVAL, "bad profile kind %d", kind);
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  long long n = 0;
+  double t = 0.0, f = 0.0;
+  for (auto& r : g_prof.recs) {
+    const bool match = (kind == 0 && r.kind == 0) || (kind == 1 && r.kind == 0 && r.dominant) || (kind == 2 && r.kind == 1);
+    if (!match) continue;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) return cuda_status(e, "profile sync");
+    float x = 0.f;
+    e = cudaEventElapsedTime(&x, r.a, r.b);
+    if (e != cudaSuccess) return cuda_status(e, "profile elapsed");
+    ++n;
+    t += x;
+    f += r.flops;
+  }
+  if (launches) *launches = n;
+  if (ms) *ms = t;
+  if (flops) *flops = f;
+  return MERA_OK;
+}

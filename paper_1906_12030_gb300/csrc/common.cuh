@@ -1,0 +1,69 @@
+// Device-side helpers shared by the library's kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "plan.h"
+
+namespace mera {
+
+// Linear index -> offset over up to kMaxLeg legs, last leg fastest.
+__device__ __forceinline__ int64_t legmap_offset(const LegMap& m, int64_t idx) {
+  int64_t off = 0;
+#pragma unroll 1
+  for (int i = m.n - 1; i >= 0; --i) {
+    const int64_t d = m.dim[i];
+    const int64_t q = idx / d;
+    off += (idx - q * d) * m.stride[i];
+    idx = q;
+  }
+  return off;
+}
+
+// Round a float to TF32 (10 explicit mantissa bits), nearest, ties away.
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Store one value into an operand buffer of precision `prec`.
+// `plane` is the element distance between the hi and lo planes (BF16X3).
+template <int PREC>
+struct OperandStore;
+
+template <>
+struct OperandStore<PREC_F64> {
+  using T = double;
+  __device__ __forceinline__ static void store(void* base, int64_t off, int64_t, double v) {
+    static_cast<double*>(base)[off] = v;
+  }
+};
+template <>
+struct OperandStore<PREC_TF32> {
+  using T = float;
+  __device__ __forceinline__ static void store(void* base, int64_t off, int64_t, double v) {
+    static_cast<float*>(base)[off] = round_tf32(float(v));
+  }
+};
+template <>
+struct OperandStore<PREC_BF16> {
+  using T = __nv_bfloat16;
+  __device__ __forceinline__ static void store(void* base, int64_t off, int64_t, double v) {
+    static_cast<__nv_bfloat16*>(base)[off] = __double2bfloat16(v);
+  }
+};
+template <>
+struct OperandStore<PREC_BF16X3> {
+  using T = __nv_bfloat16;
+  __device__ __forceinline__ static void store(void* base, int64_t off, int64_t plane, double v) {
+    const __nv_bfloat16 hi = __double2bfloat16(v);
+    const __nv_bfloat16 lo = __double2bfloat16(v - double(__bfloat162float(hi)));
+    static_cast<__nv_bfloat16*>(base)[off] = hi;
+    static_cast<__nv_bfloat16*>(base)[off + plane] = lo;
+  }
+};
+
+}  // namespace mera

@@ -1,0 +1,56 @@
+// Launchers of the library's CUDA kernels (host-side declarations).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "plan.h"
+
+#include <atomic>
+
+namespace mera {
+
+// Kernel launches issued by the library (all kernels, all devices).
+extern std::atomic<long long> g_launch_count;
+inline void count_launch(long long n = 1) { g_launch_count.fetch_add(n, std::memory_order_relaxed); }
+
+// Input tensor -> operand layout, cast to the operand precision.
+cudaError_t launch_permute(const PermuteStep& p, const double* src, void* dst, int64_t plane_elems,
+                           int prec, cudaStream_t stream);
+
+// FP64 GEMM with a scattered epilogue:
+//   C[m_dst(m) + n_dst(n)] (+)= alpha * sum_k A[m*a_m + k*a_k] * B[n*b_n + k*b_k]
+struct GemmF64Args {
+  const double* A;
+  int64_t a_m, a_k;
+  const double* B;
+  int64_t b_n, b_k;
+  int64_t M, N, K;
+  double* C;
+  LegMap m_dst, n_dst;
+  double alpha;
+  int accumulate;
+};
+cudaError_t launch_gemm_f64(const GemmF64Args& args, cudaStream_t stream);
+
+// Number of per-block partial sums the reduction kernels below may write.
+constexpr int kMaxPartials = 65536;
+
+// *out = sum_ij A[i,j] * B[j,i] for n x n row-major A, B (deterministic).
+cudaError_t launch_dot_transposed(const double* A, const double* B, int64_t n, double* partials,
+                                  double* out, cudaStream_t stream);
+
+// rho <- (X + X^T) / (2 tr X); *resid = ||rho_new - rho_old||_F (deterministic).
+// `scalars` holds 2 doubles of scratch.
+cudaError_t launch_sym_normalize(const double* X, double* rho, int64_t n, double* partials,
+                                 double* scalars, double* resid, cudaStream_t stream);
+
+// Polar-iteration helpers (all binary64, deterministic reductions).
+cudaError_t launch_frob_scale(const double* src, double* dst, int64_t count, double* partials,
+                              double* scalars, cudaStream_t stream);
+cudaError_t launch_ns_combine(const double* G, double* Bm, int64_t n, double* partials, double* resid,
+                              cudaStream_t stream);
+cudaError_t launch_scale_copy(const double* src, double* dst, int64_t count, double alpha,
+                              cudaStream_t stream);
+
+}  // namespace mera

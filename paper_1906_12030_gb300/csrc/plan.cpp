@@ -1,0 +1,547 @@
+// Contraction planner: diagram definitions, pairwise order, operand layouts.
+#include "plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <functional>
+#include <limits>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <tuple>
+
+namespace mera {
+
+int elem_bytes(int prec) {
+  switch (prec) {
+    case PREC_F64: return 8;
+    case PREC_TF32: return 4;
+    default: return 2;
+  }
+}
+int planes(int prec) { return prec == PREC_BF16X3 ? 2 : 1; }
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Diagrams.  Leg letters: the upper legs of the isometries (p q r on the ket
+// side, s t v on the bra side) have size chi_t, every other leg chi_b.
+//   ket isometries   w[x,a,p] w[b,c,q] w[d,y,r]
+//   bra isometries   w[x,A,s] w[B,C,t] w[D,y,v]
+//   even position    u[e,i,a,b] u[j,k,c,d]  h[i,j,k,l,m,n]  u[e,l,A,B] u[m,n,C,D]
+//   odd position     u[i,j,a,b] u[k,e,c,d]  h[i,j,k,l,m,n]  u[l,m,A,B] u[n,e,C,D]
+// The density rho closes E = tr(A(h) rho) as rho[s,t,v,p,q,r].
+// ---------------------------------------------------------------------------
+struct TensorSpec {
+  int slot;
+  const char* legs;
+};
+struct Diagram {
+  std::vector<TensorSpec> tensors;
+  const char* out;
+};
+
+const char* kKetW[3] = {"xap", "bcq", "dyr"};
+const char* kBraW[3] = {"xAs", "BCt", "Dyv"};
+const char* kKetU[2][2] = {{"eiab", "jkcd"}, {"ijab", "kecd"}};  // even, odd
+const char* kBraU[2][2] = {{"elAB", "mnCD"}, {"lmAB", "neCD"}};
+
+std::vector<Diagram> diagrams_of(int op) {
+  std::vector<Diagram> out;
+  for (int cs = 0; cs < 2; ++cs) {
+    if (op == OP_ASCEND || op == OP_DESCEND) {
+      Diagram d;
+      for (int k = 0; k < 3; ++k) d.tensors.push_back({SLOT_W, kKetW[k]});
+      for (int k = 0; k < 2; ++k) d.tensors.push_back({SLOT_U, kKetU[cs][k]});
+      if (op == OP_ASCEND) d.tensors.push_back({SLOT_OP, "ijklmn"});
+      for (int k = 0; k < 2; ++k) d.tensors.push_back({SLOT_U, kBraU[cs][k]});
+      for (int k = 0; k < 3; ++k) d.tensors.push_back({SLOT_W, kBraW[k]});
+      if (op == OP_DESCEND) d.tensors.push_back({SLOT_RHO, "pqrstv"});
+      d.out = (op == OP_ASCEND) ? "pqrstv" : "ijklmn";
+      out.push_back(d);
+    } else {
+      const int holes = (op == OP_ENV_W) ? 3 : 2;
+      for (int hole = 0; hole < holes; ++hole) {
+        Diagram d;
+        for (int k = 0; k < 3; ++k) d.tensors.push_back({SLOT_W, kKetW[k]});
+        for (int k = 0; k < 2; ++k) d.tensors.push_back({SLOT_U, kKetU[cs][k]});
+        d.tensors.push_back({SLOT_OP, "ijklmn"});
+        for (int k = 0; k < 2; ++k)
+          if (!(op == OP_ENV_U && k == hole)) d.tensors.push_back({SLOT_U, kBraU[cs][k]});
+        for (int k = 0; k < 3; ++k)
+          if (!(op == OP_ENV_W && k == hole)) d.tensors.push_back({SLOT_W, kBraW[k]});
+        d.tensors.push_back({SLOT_RHO, "stvpqr"});
+        d.out = (op == OP_ENV_W) ? kBraW[hole] : kBraU[cs][hole];
+        out.push_back(d);
+      }
+    }
+  }
+  return out;
+}
+
+int label_id(char c) {
+  if (c >= 'a' && c <= 'z') return c - 'a';
+  return 26 + (c - 'A');
+}
+char label_char(int id) { return id < 26 ? char('a' + id) : char('A' + id - 26); }
+
+// ---------------------------------------------------------------------------
+// Pairwise order by dynamic programming over subsets of the input tensors.
+// ---------------------------------------------------------------------------
+struct Node {
+  int left = -1, right = -1;  // children (node ids) or -1 for a leaf
+  int tensor = -1;            // leaf: input tensor index
+  uint64_t legs = 0;          // open legs (label bitmask)
+};
+
+struct Tree {
+  std::vector<Node> nodes;
+  int root = -1;
+};
+
+double size_of(uint64_t legs, const int64_t* dim) {
+  double s = 1.0;
+  for (int l = 0; l < 64; ++l)
+    if (legs >> l & 1ull) s *= double(dim[l]);
+  return s;
+}
+
+int popcount64(uint64_t x) { return __builtin_popcountll(x); }
+
+Tree plan_order(const std::vector<uint64_t>& tmask, const int64_t* dim, int max_rank) {
+  const int n = int(tmask.size());
+  const uint32_t full = (1u << n) - 1;
+  std::vector<uint64_t> open(1u << n, 0);
+  for (uint32_t s = 1; s <= full; ++s) {
+    int low = __builtin_ctz(s);
+    open[s] = open[s & (s - 1)] ^ tmask[low];
+  }
+  const double inf = std::numeric_limits<double>::infinity();
+  std::vector<double> cost(1u << n, inf), peak(1u << n, 0.0);
+  std::vector<uint32_t> split(1u << n, 0);
+  for (int t = 0; t < n; ++t) {
+    cost[1u << t] = 0.0;
+    peak[1u << t] = 0.0;
+  }
+  std::vector<uint32_t> order;
+  for (uint32_t s = 1; s <= full; ++s) order.push_back(s);
+  std::stable_sort(order.begin(), order.end(),
+                   [](uint32_t a, uint32_t b) { return __builtin_popcount(a) < __builtin_popcount(b); });
+  for (uint32_t s : order) {
+    if (__builtin_popcount(s) < 2) continue;
+    if (popcount64(open[s]) > max_rank && s != full) continue;
+    const uint32_t low = s & (~s + 1);
+    const double out_size = size_of(open[s], dim);
+    for (uint32_t s1 = (s - 1) & s; s1; s1 = (s1 - 1) & s) {
+      if (!(s1 & low)) continue;  // each unordered split once
+      const uint32_t s2 = s ^ s1;
+      if (cost[s1] == inf || cost[s2] == inf) continue;
+      const uint64_t shared = open[s1] & open[s2];
+      if (!shared) continue;  // no outer products
+      const double fl = 2.0 * size_of(open[s1] | open[s2], dim);
+      const double c = cost[s1] + cost[s2] + fl;
+      const double pk = std::max({peak[s1], peak[s2], s == full ? 0.0 : out_size});
+      const bool better = c < cost[s] * (1 - 1e-12) ||
+                          (c <= cost[s] * (1 + 1e-12) && pk < peak[s]);
+      if (better) {
+        cost[s] = c;
+        peak[s] = pk;
+        split[s] = s1;
+      }
+    }
+  }
+  Tree tr;
+  if (cost[full] == inf) return tr;
+  // Build nodes recursively.
+  std::vector<std::pair<uint32_t, int>> stack;
+  std::map<uint32_t, int> id_of;
+  std::function<int(uint32_t)> build = [&](uint32_t s) -> int {
+    Node nd;
+    nd.legs = open[s];
+    if (__builtin_popcount(s) == 1) {
+      nd.tensor = __builtin_ctz(s);
+      tr.nodes.push_back(nd);
+      return int(tr.nodes.size()) - 1;
+    }
+    const int l = build(split[s]);
+    const int r = build(s ^ split[s]);
+    nd.left = l;
+    nd.right = r;
+    tr.nodes.push_back(nd);
+    return int(tr.nodes.size()) - 1;
+  };
+  tr.root = build(full);
+  return tr;
+}
+
+// ---------------------------------------------------------------------------
+// Layouts.
+// ---------------------------------------------------------------------------
+std::vector<int> legs_list(uint64_t m) {
+  std::vector<int> v;
+  for (int l = 0; l < 64; ++l)
+    if (m >> l & 1ull) v.push_back(l);
+  return v;
+}
+
+std::string legs_str(const std::vector<int>& v) {
+  std::string s;
+  for (int l : v) s.push_back(label_char(l));
+  return s;
+}
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct Builder {
+  const Diagram& dg;
+  const int64_t* dim;
+  int prec;
+  double alpha;
+  int accumulate;
+  Tree tr;
+  Program prog;
+  // For every node: the layout its consumer wants (stride of every leg in
+  // elements) and the operand buffer it lives in.
+  std::vector<std::map<int, int64_t>> dst_stride;
+  std::vector<int> buf_of;
+  // GEMM info per internal node
+  struct G {
+    int a = -1, b = -1;
+    std::vector<int> mlegs, nlegs, klegs;
+  };
+  std::vector<G> g;
+
+  Builder(const Diagram& d, const int64_t* dm, int p, double al, int acc)
+      : dg(d), dim(dm), prec(p), alpha(al), accumulate(acc) {}
+
+  int64_t prod(const std::vector<int>& legs) const {
+    int64_t s = 1;
+    for (int l : legs) s *= dim[l];
+    return s;
+  }
+
+  LegMap legmap(const std::vector<int>& legs, const std::map<int, int64_t>& stride) const {
+    LegMap m;
+    m.n = int(legs.size());
+    for (int i = 0; i < m.n; ++i) {
+      m.dim[i] = dim[legs[i]];
+      m.stride[i] = stride.at(legs[i]);
+    }
+    return m;
+  }
+
+  // Operand layout [free..., k...] row-major with padded row pitch.
+  std::map<int, int64_t> operand_strides(const std::vector<int>& free, const std::vector<int>& k,
+                                         int64_t ld) const {
+    std::map<int, int64_t> st;
+    int64_t s = 1;
+    for (int i = int(k.size()) - 1; i >= 0; --i) {
+      st[k[i]] = s;
+      s *= dim[k[i]];
+    }
+    s = ld;
+    for (int i = int(free.size()) - 1; i >= 0; --i) {
+      st[free[i]] = s;
+      s *= dim[free[i]];
+    }
+    return st;
+  }
+
+  int64_t pitch(int64_t cols) const {
+    const int64_t align = std::max<int64_t>(1, 16 / elem_bytes(prec));
+    return round_up(std::max<int64_t>(cols, 1), align);
+  }
+
+  bool build() {
+    const int n = int(dg.tensors.size());
+    std::vector<uint64_t> tmask(n, 0);
+    for (int t = 0; t < n; ++t)
+      for (const char* c = dg.tensors[t].legs; *c; ++c) tmask[t] |= 1ull << label_id(*c);
+    tr = plan_order(tmask, dim, 7);
+    if (tr.root < 0) return false;
+    const size_t nn = tr.nodes.size();
+    dst_stride.assign(nn, {});
+    buf_of.assign(nn, -1);
+    g.assign(nn, {});
+    // GEMM roles (bottom-up information only depends on leg sets).
+    for (size_t i = 0; i < nn; ++i) {
+      const Node& nd = tr.nodes[i];
+      if (nd.tensor >= 0) continue;
+      const uint64_t L = tr.nodes[nd.left].legs, R = tr.nodes[nd.right].legs;
+      const uint64_t K = L & R;
+      const double fl = size_of(L & ~K, dim), fr = size_of(R & ~K, dim);
+      G& gi = g[i];
+      gi.a = (fl >= fr) ? nd.left : nd.right;
+      gi.b = (fl >= fr) ? nd.right : nd.left;
+      gi.klegs = legs_list(K);
+    }
+    // Root output layout: the caller's order of the open legs.
+    {
+      std::vector<int> out;
+      for (const char* c = dg.out; *c; ++c) out.push_back(label_id(*c));
+      int64_t s = 1;
+      for (int i = int(out.size()) - 1; i >= 0; --i) {
+        dst_stride[tr.root][out[i]] = s;
+        s *= dim[out[i]];
+      }
+      prog.out_rank = int(out.size());
+    }
+    // Top-down: fix orders and operand layouts, then emit steps bottom-up.
+    std::vector<int> topo;  // pre-order
+    std::vector<int> st{tr.root};
+    while (!st.empty()) {
+      int i = st.back();
+      st.pop_back();
+      topo.push_back(i);
+      if (tr.nodes[i].tensor < 0) {
+        st.push_back(tr.nodes[i].left);
+        st.push_back(tr.nodes[i].right);
+      }
+    }
+    for (int i : topo) {
+      const Node& nd = tr.nodes[i];
+      if (nd.tensor >= 0) continue;
+      G& gi = g[i];
+      const uint64_t K = tr.nodes[gi.a].legs & tr.nodes[gi.b].legs;
+      std::vector<int> mlegs = legs_list(tr.nodes[gi.a].legs & ~K);
+      std::vector<int> nlegs = legs_list(tr.nodes[gi.b].legs & ~K);
+      auto by_stride = [&](int x, int y) { return dst_stride[i].at(x) > dst_stride[i].at(y); };
+      std::stable_sort(mlegs.begin(), mlegs.end(), by_stride);
+      std::stable_sort(nlegs.begin(), nlegs.end(), by_stride);
+      // Contracted-leg order: make the innermost one a row leg of the A
+      // child's own GEMM when that child is an intermediate, so that the
+      // child's epilogue writes consecutive addresses from consecutive rows.
+      std::vector<int> klegs = gi.klegs;
+      int prefer = -1;
+      for (int c : {gi.a, gi.b}) {
+        if (tr.nodes[c].tensor >= 0) continue;
+        const G& gc = g[c];
+        const uint64_t Kc = tr.nodes[gc.a].legs & tr.nodes[gc.b].legs;
+        const uint64_t rows_c = tr.nodes[gc.a].legs & ~Kc;
+        for (int l : klegs)
+          if (rows_c >> l & 1ull) { prefer = l; break; }
+        if (prefer >= 0) break;
+      }
+      if (prefer >= 0) {
+        klegs.erase(std::find(klegs.begin(), klegs.end(), prefer));
+        klegs.push_back(prefer);
+      }
+      gi.mlegs = mlegs;
+      gi.nlegs = nlegs;
+      gi.klegs = klegs;
+      const int64_t Kn = prod(klegs);
+      const int64_t ld = pitch(Kn);
+      dst_stride[gi.a] = operand_strides(mlegs, klegs, ld);
+      dst_stride[gi.b] = operand_strides(nlegs, klegs, ld);
+      // operand buffers for both children
+      for (int c : {gi.a, gi.b}) {
+        Buffer b;
+        b.rows = (c == gi.a) ? prod(mlegs) : prod(nlegs);
+        b.ld = ld;
+        b.plane_bytes = round_up(b.rows * ld * elem_bytes(prec), 256);
+        b.bytes = b.plane_bytes * planes(prec);
+        prog.bufs.push_back(b);
+        buf_of[c] = int(prog.bufs.size()) - 1;
+      }
+    }
+    // Emit steps in post-order (children first).
+    std::vector<int> post(topo.rbegin(), topo.rend());
+    // reverse pre-order (root, right, left) gives a valid post-order.
+    std::vector<int> first_use(prog.bufs.size(), -1), last_use(prog.bufs.size(), -1);
+    for (int i : post) {
+      const Node& nd = tr.nodes[i];
+      if (nd.tensor >= 0) {
+        const TensorSpec& ts = dg.tensors[nd.tensor];
+        const G* parent_g = nullptr;
+        (void)parent_g;
+        Step s;
+        s.kind = 0;
+        PermuteStep& p = s.p;
+        p.slot = ts.slot;
+        p.dst_buf = buf_of[i];
+        // which legs are rows vs cols of the destination: decided by strides
+        // (cols = legs with stride < ld).
+        const Buffer& b = prog.bufs[p.dst_buf];
+        std::vector<std::pair<int64_t, int>> legs;  // (dst stride, label)
+        for (const char* c = ts.legs; *c; ++c) legs.push_back({dst_stride[i].at(label_id(*c)), label_id(*c)});
+        std::sort(legs.begin(), legs.end(), [](auto& x, auto& y) { return x.first > y.first; });
+        // source strides: the tensor's own row-major order
+        std::map<int, int64_t> src;
+        {
+          int64_t sstr = 1;
+          const int nl = int(std::char_traits<char>::length(ts.legs));
+          for (int q = nl - 1; q >= 0; --q) {
+            src[label_id(ts.legs[q])] = sstr;
+            sstr *= dim[label_id(ts.legs[q])];
+          }
+        }
+        std::vector<int> rl, cl;
+        for (auto& pr : legs) (pr.first >= b.ld ? rl : cl).push_back(pr.second);
+        p.rows = prod(rl);
+        p.cols = prod(cl);
+        p.ld = b.ld;
+        p.row_src = legmap(rl, src);
+        p.col_src = legmap(cl, src);
+        prog.steps.push_back(s);
+        const int si = int(prog.steps.size()) - 1;
+        first_use[p.dst_buf] = si;
+        continue;
+      }
+      const G& gi = g[i];
+      Step s;
+      s.kind = 1;
+      GemmStep& gs = s.g;
+      gs.a_buf = buf_of[gi.a];
+      gs.b_buf = buf_of[gi.b];
+      gs.M = prod(gi.mlegs);
+      gs.N = prod(gi.nlegs);
+      gs.K = prod(gi.klegs);
+      gs.lda = prog.bufs[gs.a_buf].ld;
+      gs.ldb = prog.bufs[gs.b_buf].ld;
+      gs.c_buf = (i == tr.root) ? -1 : buf_of[i];
+      gs.c_ld = (i == tr.root) ? 0 : prog.bufs[buf_of[i]].ld;
+      gs.m_dst = legmap(gi.mlegs, dst_stride[i]);
+      gs.n_dst = legmap(gi.nlegs, dst_stride[i]);
+      gs.alpha = (i == tr.root) ? alpha : 1.0;
+      gs.accumulate = (i == tr.root) ? accumulate : 0;
+      gs.flops = 2.0 * double(gs.M) * double(gs.N) * double(gs.K);
+      {
+        std::vector<int> kl = gi.klegs;
+        auto a_legs = gi.mlegs;
+        a_legs.insert(a_legs.end(), kl.begin(), kl.end());
+        auto b_legs = gi.nlegs;
+        b_legs.insert(b_legs.end(), kl.begin(), kl.end());
+        std::vector<std::pair<int64_t, int>> o;
+        for (int l : gi.mlegs) o.push_back({dst_stride[i].at(l), l});
+        for (int l : gi.nlegs) o.push_back({dst_stride[i].at(l), l});
+        std::sort(o.begin(), o.end(), [](auto& x, auto& y) { return x.first > y.first; });
+        std::vector<int> ol;
+        for (auto& pr : o) ol.push_back(pr.second);
+        gs.label = legs_str(a_legs) + "*" + legs_str(b_legs) + "->" + legs_str(ol);
+      }
+      prog.flops += gs.flops;
+      prog.steps.push_back(s);
+      const int si = int(prog.steps.size()) - 1;
+      last_use[gs.a_buf] = si;
+      last_use[gs.b_buf] = si;
+      if (gs.c_buf >= 0) first_use[gs.c_buf] = si;
+    }
+    double fmax = 0.0;
+    for (const Step& st : prog.steps)
+      if (st.kind == 1) fmax = std::max(fmax, st.g.flops);
+    for (Step& st : prog.steps)
+      if (st.kind == 1) st.g.dominant = st.g.flops >= 0.25 * fmax;
+    // Arena: first-fit over [first_use, last_use] intervals.
+    struct Iv { int64_t off, bytes; int lo, hi; };
+    std::vector<Iv> placed;
+    size_t top = 0;
+    for (size_t bi = 0; bi < prog.bufs.size(); ++bi) {
+      Buffer& b = prog.bufs[bi];
+      const int lo = first_use[bi], hi = last_use[bi];
+      std::vector<std::pair<int64_t, int64_t>> busy;
+      for (auto& iv : placed)
+        if (!(iv.hi < lo || hi < iv.lo)) busy.push_back({iv.off, iv.off + iv.bytes});
+      std::sort(busy.begin(), busy.end());
+      int64_t off = 0;
+      for (auto& r : busy) {
+        if (off + b.bytes <= r.first) break;
+        off = std::max(off, r.second);
+      }
+      b.offset = off;
+      placed.push_back({off, b.bytes, lo, hi});
+      top = std::max<size_t>(top, size_t(off + b.bytes));
+    }
+    prog.ws_bytes = top;
+    return true;
+  }
+};
+
+struct Key {
+  int op, chi_b, chi_t, prec;
+  bool operator<(const Key& o) const {
+    return std::tie(op, chi_b, chi_t, prec) < std::tie(o.op, o.chi_b, o.chi_t, o.prec);
+  }
+};
+
+std::mutex g_mu;
+std::map<Key, std::unique_ptr<OpProgram>> g_cache;
+
+}  // namespace
+
+const OpProgram* get_program(int op, int chi_b, int chi_t, int prec) {
+  if (op < OP_ASCEND || op > OP_ENV_W) return nullptr;
+  if (prec < PREC_F64 || prec > PREC_BF16X3) return nullptr;
+  if (chi_b < 1 || chi_t < 1 || chi_b > 64 || chi_t > 64) return nullptr;
+  if (chi_t > chi_b * chi_b) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Key k{op, chi_b, chi_t, prec};
+  auto it = g_cache.find(k);
+  if (it != g_cache.end()) return it->second.get();
+  int64_t dim[64];
+  for (int l = 0; l < 64; ++l) dim[l] = chi_b;
+  for (char c : std::string("pqrstv")) dim[label_id(c)] = chi_t;
+  auto prog = std::make_unique<OpProgram>();
+  const std::vector<Diagram> ds = diagrams_of(op);
+  for (size_t d = 0; d < ds.size(); ++d) {
+    Builder b(ds[d], dim, prec, 0.5, d == 0 ? 0 : 1);
+    if (!b.build()) return nullptr;
+    prog->ws_bytes = std::max(prog->ws_bytes, b.prog.ws_bytes);
+    prog->flops += b.prog.flops;
+    prog->diagrams.push_back(std::move(b.prog));
+  }
+  const OpProgram* out = prog.get();
+  g_cache[k] = std::move(prog);
+  return out;
+}
+
+std::string program_json(const OpProgram& prog, int op, int chi_b, int chi_t, int prec) {
+  std::ostringstream o;
+  o.precision(17);
+  auto lm = [&](const LegMap& m) {
+    o << "{\"dim\":[";
+    for (int i = 0; i < m.n; ++i) o << (i ? "," : "") << m.dim[i];
+    o << "],\"stride\":[";
+    for (int i = 0; i < m.n; ++i) o << (i ? "," : "") << m.stride[i];
+    o << "]}";
+  };
+  o << "{\"op\":" << op << ",\"chi_b\":" << chi_b << ",\"chi_t\":" << chi_t << ",\"prec\":" << prec
+    << ",\"ws_bytes\":" << prog.ws_bytes << ",\"flops\":" << prog.flops << ",\"elem_bytes\":" << elem_bytes(prec)
+    << ",\"planes\":" << planes(prec) << ",\"diagrams\":[";
+  for (size_t d = 0; d < prog.diagrams.size(); ++d) {
+    const Program& p = prog.diagrams[d];
+    o << (d ? "," : "") << "{\"ws_bytes\":" << p.ws_bytes << ",\"flops\":" << p.flops << ",\"bufs\":[";
+    for (size_t b = 0; b < p.bufs.size(); ++b)
+      o << (b ? "," : "") << "{\"rows\":" << p.bufs[b].rows << ",\"ld\":" << p.bufs[b].ld
+        << ",\"offset\":" << p.bufs[b].offset << ",\"bytes\":" << p.bufs[b].bytes << "}";
+    o << "],\"steps\":[";
+    for (size_t s = 0; s < p.steps.size(); ++s) {
+      const Step& st = p.steps[s];
+      o << (s ? "," : "");
+      if (st.kind == 0) {
+        o << "{\"kind\":\"permute\",\"slot\":" << st.p.slot << ",\"dst_buf\":" << st.p.dst_buf
+          << ",\"rows\":" << st.p.rows << ",\"cols\":" << st.p.cols << ",\"ld\":" << st.p.ld << ",\"row_src\":";
+        lm(st.p.row_src);
+        o << ",\"col_src\":";
+        lm(st.p.col_src);
+        o << "}";
+      } else {
+        const GemmStep& g = st.g;
+        o << "{\"kind\":\"gemm\",\"label\":\"" << g.label << "\",\"a_buf\":" << g.a_buf << ",\"b_buf\":" << g.b_buf
+          << ",\"M\":" << g.M << ",\"N\":" << g.N << ",\"K\":" << g.K << ",\"lda\":" << g.lda << ",\"ldb\":" << g.ldb
+          << ",\"c_buf\":" << g.c_buf << ",\"alpha\":" << g.alpha << ",\"accumulate\":" << g.accumulate
+          << ",\"flops\":" << g.flops << ",\"dominant\":" << g.dominant << ",\"m_dst\":";
+        lm(g.m_dst);
+        o << ",\"n_dst\":";
+        lm(g.n_dst);
+        o << "}";
+      }
+    }
+    o << "]}";
+  }
+  o << "]}";
+  return o.str();
+}
+
+}  // namespace mera

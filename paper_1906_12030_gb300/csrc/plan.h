@@ -1,0 +1,96 @@
+// Contraction programs of the binary-MERA diagrams (Fig. 4, Fig. A1).
+//
+// Each diagram is a closed tensor network with a few open legs.  The planner
+// picks a pairwise contraction order by exhaustive dynamic programming over
+// subsets (minimum flops, intermediates of rank <= 7), then fixes the memory
+// layout of every intermediate so that its consumer reads it as a plain
+// row-major matrix [free legs | contracted legs].  The producing GEMM writes
+// its result straight into that layout (a scatter epilogue), so no transpose
+// pass runs between contractions; only the caller's input tensors are copied
+// once into operand layout (fused with the cast to the operand precision).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace mera {
+
+enum Prec : int { PREC_F64 = 0, PREC_TF32 = 1, PREC_BF16 = 2, PREC_BF16X3 = 3 };
+enum Slot : int { SLOT_OP = 0, SLOT_RHO = 1, SLOT_U = 2, SLOT_W = 3 };
+enum Op : int { OP_ASCEND = 0, OP_DESCEND = 1, OP_ENV_U = 2, OP_ENV_W = 3 };
+
+constexpr int kMaxLeg = 8;
+
+// Linear index -> element offset.  The index is decomposed over `n` legs,
+// the last leg varying fastest; offset = sum idx_l * stride_l.
+struct LegMap {
+  int n = 0;
+  int64_t dim[kMaxLeg] = {};
+  int64_t stride[kMaxLeg] = {};
+};
+
+// Copy (and cast) an input tensor into operand layout:
+// dst[r * ld + c] = src[row_src(r) + col_src(c)],  r < rows, c < cols.
+struct PermuteStep {
+  int slot = 0;
+  int dst_buf = 0;
+  int64_t rows = 0, cols = 0, ld = 0;
+  LegMap row_src, col_src;
+};
+
+// C[m, n] (+)= alpha * sum_k A[m*lda + k] * B[n*ldb + k], scattered to
+// dst + m_dst(m) + n_dst(n).  c_buf == -1 targets the caller's output.
+struct GemmStep {
+  int a_buf = 0, b_buf = 0;
+  int64_t M = 1, N = 1, K = 1, lda = 1, ldb = 1;
+  int c_buf = -1;
+  int64_t c_ld = 0;  // row pitch of the destination when it is an operand buffer
+  LegMap m_dst, n_dst;
+  double alpha = 1.0;
+  int accumulate = 0;
+  double flops = 0.0;
+  int dominant = 0;   // one of the chi^9-class steps of its diagram
+  std::string label;  // e.g. "aceiq*CDcdil->ADadelq" for inspection
+};
+
+struct Step {
+  int kind = 0;  // 0 permute, 1 gemm
+  PermuteStep p;
+  GemmStep g;
+};
+
+struct Buffer {
+  int64_t rows = 0, ld = 0;   // operand matrix rows x pitch (elements per plane)
+  int64_t offset = 0;         // byte offset in the workspace
+  int64_t plane_bytes = 0;    // bytes of one plane (BF16X3 keeps hi, then lo)
+  int64_t bytes = 0;          // plane_bytes * planes
+};
+
+// The program of one diagram.  Buffers are laid out in one arena.
+struct Program {
+  std::vector<Step> steps;
+  std::vector<Buffer> bufs;
+  size_t ws_bytes = 0;
+  double flops = 0.0;
+  int out_rank = 0;
+};
+
+// A whole operation (sum of diagrams, each scaled by alpha, the first one
+// overwriting the output and the others accumulating).
+struct OpProgram {
+  std::vector<Program> diagrams;
+  size_t ws_bytes = 0;
+  double flops = 0.0;
+};
+
+int elem_bytes(int prec);   // storage bytes of one operand element (one plane)
+int planes(int prec);       // 2 for BF16X3 (hi, lo), else 1
+
+// Builds (and caches) the program; thread safe.  Returns nullptr on bad input.
+const OpProgram* get_program(int op, int chi_b, int chi_t, int prec);
+
+std::string program_json(const OpProgram& prog, int op, int chi_b, int chi_t, int prec);
+
+}  // namespace mera

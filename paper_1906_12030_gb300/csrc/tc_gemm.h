@@ -1,0 +1,35 @@
+// Tensor-core (tcgen05 / TMEM / TMA) GEMM of the contraction programs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "plan.h"
+
+namespace mera {
+
+// C[m_dst(m) + n_dst(n)] (+)= alpha * sum_k A[m, k] * B[n, k]
+// A: M x K operand matrix with row pitch lda elements (one or two planes),
+// B: N x K with pitch ldb.  Operands are TF32 (stored as FP32), BF16, or a
+// BF16 hi/lo pair (BF16X3: the lo plane follows the hi plane at
+// *_plane_bytes).  FP32 accumulation in tensor memory.  The destination is
+// either the caller's FP64 output (c_final) or the next operand buffer in
+// the same precision (c_plane_elems apart for the lo plane).
+struct TcGemmArgs {
+  int prec = 0;
+  const void* A = nullptr;
+  int64_t a_plane_bytes = 0, lda = 0;
+  const void* B = nullptr;
+  int64_t b_plane_bytes = 0, ldb = 0;
+  int64_t M = 0, N = 0, K = 0;
+  bool c_final = true;
+  void* C = nullptr;
+  int64_t c_plane_elems = 0;
+  LegMap m_dst, n_dst;
+  double alpha = 1.0;
+  int accumulate = 0;
+};
+
+cudaError_t launch_gemm_tc(const TcGemmArgs& args, cudaStream_t stream);
+
+}  // namespace mera

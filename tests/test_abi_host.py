@@ -1,0 +1,163 @@
+"""Host-side tests of the C-ABI library (no GPU needed).
+
+* the shared library builds for sm_103a, loads and exports every entry point
+  that include/mera.h declares;
+* host-only entry points (Hamiltonian builder, planner, flop counts,
+  argument checks) behave as documented;
+* the contraction programs the planner emits -- pairwise orders, operand
+  layouts, padded pitches, scattered epilogue strides, workspace arena --
+  reproduce the oracle when executed step by step with numpy exactly as the
+  kernels execute them.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import mera_inputs as I
+from oracle import mera_oracle as O
+
+m = pytest.importorskip("paper_1906_12030_gb300")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mera.h")
+
+
+def _declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:mera_status|const char\*|long long)\s+(mera_\w+)\s*\(", text, re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = m.library()
+    names = _declared_symbols()
+    assert len(names) >= 16
+    for name in names:
+        assert hasattr(lib, name), name
+    assert "sm_103a" in m.mera_version()
+
+
+def test_ising_builder_matches_oracle():
+    for hz in (1.0, 0.9, 1.1):
+        h1, s = m.mera_ising_h1(hz)
+        h1o, so = O.ising_h1(hz)
+        assert abs(s - so) < 1e-13
+        assert np.abs(h1 - h1o).max() < 1e-13
+
+
+def test_argument_checks_without_device():
+    with pytest.raises(m.MeraError):
+        m.mera_workspace_size(99, 4, 4, 0)
+    with pytest.raises(m.MeraError):
+        m.mera_workspace_size(m.OP_ASCEND, 4, 17, 0)  # chi_t > chi_b^2
+    with pytest.raises(m.MeraError):
+        m.mera_workspace_size(m.OP_ASCEND, 0, 4, 0)
+    with pytest.raises(m.MeraError):
+        m.mera_workspace_size(m.OP_FIXED_POINT, 4, 3, 0)
+    with pytest.raises(m.MeraError):
+        m.mera_polar_workspace_size(3, 4)  # m < n
+    assert m.mera_workspace_size(m.OP_ASCEND, 4, 4, m.PREC_BF16X3) > 0
+
+
+@pytest.mark.parametrize("chi,per_diagram", [(4, 1.59e6), (8, 6.72e8), (16, 3.09e11), (32, 1.50e14)])
+def test_min_flop_orders(chi, per_diagram):
+    """4 chi^9 + 8 chi^8 + lower per diagram: the chi^9 cost of Sec. II B."""
+    for op, nd in ((m.OP_ASCEND, 2), (m.OP_DESCEND, 2), (m.OP_ENV_U, 4), (m.OP_ENV_W, 6)):
+        f = m.mera_flops(op, chi, chi)
+        assert f / nd == pytest.approx(per_diagram, rel=0.01)
+        assert f / nd >= 4 * chi ** 9
+
+
+def test_sweep_flops_chi16():
+    """tau* = 3, 20 power steps: 50 SI diagrams + 14 + 14, ~1.98e13 at chi = 16."""
+    dims = I.layer_dims(16)
+    total = 0.0
+    for k, (cb, ct) in enumerate(dims):
+        if k < len(dims) - 1:
+            total += m.mera_flops(m.OP_ASCEND, cb, ct)
+        else:
+            total += 20 * m.mera_flops(m.OP_DESCEND, cb, ct)
+        total += m.mera_flops(m.OP_ENV_U, cb, ct) + m.mera_flops(m.OP_ENV_W, cb, ct)
+        if 0 < k < len(dims) - 1:
+            total += m.mera_flops(m.OP_DESCEND, cb, ct)  # rho down one transitional layer
+        elif k == 0:
+            total += m.mera_flops(m.OP_ASCEND, cb, ct)   # energy tr(A(h1) rho2)
+    assert total == pytest.approx(1.98e13, rel=0.01)
+
+
+# --------------------------------------------------------------------------
+# Emulate the programs with numpy.
+# --------------------------------------------------------------------------
+def _offsets(lm, count):
+    idx = np.arange(count, dtype=np.int64)
+    off = np.zeros(count, dtype=np.int64)
+    for d, s in zip(reversed(lm["dim"]), reversed(lm["stride"])):
+        off += (idx % d) * s
+        idx //= d
+    return off
+
+
+def _emulate(plan, inputs, out_size):
+    """Run a program in float64; buffers live in one flat arena (per plane)."""
+    eb = plan["elem_bytes"]
+    out = np.zeros(out_size)
+    arena = np.full(plan["ws_bytes"] // eb + 1, np.nan)
+    for dg in plan["diagrams"]:
+        bufs = dg["bufs"]
+        for b in bufs:
+            assert b["offset"] % 256 == 0
+            assert b["ld"] * eb % 16 == 0  # TMA: row pitch multiple of 16 bytes
+            assert b["offset"] + b["bytes"] <= plan["ws_bytes"]
+        arena[:] = np.nan  # stale data from an earlier diagram must never be read
+        for st in dg["steps"]:
+            if st["kind"] == "permute":
+                src = inputs[st["slot"]].reshape(-1)
+                b = bufs[st["dst_buf"]]
+                rows, cols, ld = st["rows"], st["cols"], st["ld"]
+                ro = _offsets(st["row_src"], rows)
+                co = _offsets(st["col_src"], cols)
+                base = b["offset"] // eb
+                dst_idx = base + (np.arange(rows)[:, None] * ld + np.arange(cols)[None, :])
+                arena[dst_idx] = src[ro[:, None] + co[None, :]]
+            else:
+                a, bb = bufs[st["a_buf"]], bufs[st["b_buf"]]
+                M, N, K = st["M"], st["N"], st["K"]
+                A = arena[a["offset"] // eb + np.arange(M)[:, None] * st["lda"] + np.arange(K)[None, :]]
+                B = arena[bb["offset"] // eb + np.arange(N)[:, None] * st["ldb"] + np.arange(K)[None, :]]
+                assert not np.isnan(A).any() and not np.isnan(B).any()
+                C = st["alpha"] * (A @ B.T)
+                mo = _offsets(st["m_dst"], M)
+                no = _offsets(st["n_dst"], N)
+                idx = mo[:, None] + no[None, :]
+                assert len(np.unique(idx)) == idx.size  # the scatter is a bijection
+                if st["c_buf"] < 0:
+                    assert idx.min() >= 0 and idx.max() < out_size
+                    if st["accumulate"]:
+                        out[idx] += C
+                    else:
+                        out[idx] = C
+                else:
+                    cb = bufs[st["c_buf"]]
+                    arena[cb["offset"] // eb + idx] = C
+    return out
+
+
+@pytest.mark.parametrize("prec", [m.PREC_F64, m.PREC_BF16X3])
+@pytest.mark.parametrize("chi_b,chi_t", [(2, 2), (3, 3), (2, 3), (4, 3), (3, 5)])
+def test_programs_reproduce_oracle(prec, chi_b, chi_t):
+    rng = np.random.default_rng(20)
+    u, w = I.random_u(rng, chi_b), I.random_w(rng, chi_b, chi_t)
+    h = I.random_operator(rng, chi_b, symmetric=False)
+    rho = I.random_operator(rng, chi_t, symmetric=False)
+    hs, rs = I.random_operator(rng, chi_b), I.random_density(rng, chi_t)
+    cases = [
+        (m.OP_ASCEND, [h, None, u, w], O.ascend(h, u, w)),
+        (m.OP_DESCEND, [None, rho, u, w], O.descend(rho, u, w)),
+        (m.OP_ENV_U, [hs, rs, u, w], O.env_u(hs, rs, u, w)),
+        (m.OP_ENV_W, [hs, rs, u, w], O.env_w(hs, rs, u, w)),
+    ]
+    for op, inputs, want in cases:
+        plan = m.mera_plan_json(op, chi_b, chi_t, prec)
+        got = _emulate(plan, inputs, want.size).reshape(want.shape)
+        assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max()), op

@@ -1,0 +1,170 @@
+"""GPU parity: every C-ABI map against the FP64 oracle on seeded inputs.
+
+FP64 mode: |gpu - oracle| <= 1e-10 * max|oracle| element by element (the
+relative-to-max-norm reading of "within 1e-10 relative").  Sizes span
+several GEMM tiles with ragged tails (chi = 5: 625-row operands) and uneven
+layer dimensions (chi_b != chi_t) as in the first two MERA layers.
+"""
+import numpy as np
+import pytest
+
+import mera_inputs as I
+from oracle import mera_oracle as O
+
+torch = pytest.importorskip("torch")
+m = pytest.importorskip("paper_1906_12030_gb300")
+
+pytestmark = pytest.mark.gpu
+
+TOL_F64 = 1e-10
+DIMS = [(2, 2), (3, 3), (4, 4), (5, 5), (2, 3), (4, 6), (4, 16), (3, 8), (8, 8)]
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _err(got, want):
+    return float(np.abs(got - want).max() / max(np.abs(want).max(), 1e-300))
+
+
+def _inputs(chi_b, chi_t, seed=0):
+    rng = np.random.default_rng(seed)
+    u, w = I.random_u(rng, chi_b), I.random_w(rng, chi_b, chi_t)
+    h = I.random_operator(rng, chi_b)
+    rho = I.random_density(rng, chi_t)
+    return u, w, h, rho
+
+
+@pytest.mark.parametrize("chi_b,chi_t", DIMS)
+def test_ascend_descend_f64(chi_b, chi_t):
+    u, w, h, rho = _inputs(chi_b, chi_t, 1)
+    hn = I.random_operator(np.random.default_rng(7), chi_b, symmetric=False)
+    out = torch.empty(chi_t ** 6, dtype=torch.float64, device="cuda")
+    m.mera_ascend(_cuda(hn).reshape(-1), _cuda(u).reshape(-1), _cuda(w).reshape(-1), chi_b, chi_t, out)
+    assert _err(out.cpu().numpy().reshape((chi_t,) * 6), O.ascend(hn, u, w)) < TOL_F64
+    out_d = torch.empty(chi_b ** 6, dtype=torch.float64, device="cuda")
+    m.mera_descend(_cuda(rho).reshape(-1), _cuda(u).reshape(-1), _cuda(w).reshape(-1), chi_b, chi_t, out_d)
+    assert _err(out_d.cpu().numpy().reshape((chi_b,) * 6), O.descend(rho, u, w)) < TOL_F64
+
+
+@pytest.mark.parametrize("chi_b,chi_t", DIMS)
+def test_environments_f64(chi_b, chi_t):
+    u, w, h, rho = _inputs(chi_b, chi_t, 2)
+    gu = torch.empty(chi_b ** 4, dtype=torch.float64, device="cuda")
+    gw = torch.empty(chi_b ** 2 * chi_t, dtype=torch.float64, device="cuda")
+    args = (_cuda(h).reshape(-1), _cuda(rho).reshape(-1), _cuda(u).reshape(-1), _cuda(w).reshape(-1), chi_b, chi_t)
+    m.mera_env_u(*args, gu)
+    m.mera_env_w(*args, gw)
+    assert _err(gu.cpu().numpy().reshape(u.shape), O.env_u(h, rho, u, w)) < TOL_F64
+    assert _err(gw.cpu().numpy().reshape(w.shape), O.env_w(h, rho, u, w)) < TOL_F64
+
+
+@pytest.mark.parametrize("chi_b,chi_t", [(3, 3), (4, 6), (5, 5)])
+def test_energy_f64(chi_b, chi_t):
+    u, w, h, rho = _inputs(chi_b, chi_t, 3)
+    e = torch.empty(1, dtype=torch.float64, device="cuda")
+    m.mera_energy(_cuda(h).reshape(-1), _cuda(rho).reshape(-1), _cuda(u).reshape(-1), _cuda(w).reshape(-1),
+                  chi_b, chi_t, e)
+    want = O.energy(h, rho, u, w)
+    assert abs(e.item() - want) <= TOL_F64 * max(1.0, abs(want))
+
+
+@pytest.mark.parametrize("chi", [2, 4, 5])
+def test_fixed_point_f64(chi):
+    u, w, _, _ = _inputs(chi, chi, 4)
+    rho0 = O.identity_density(chi)
+    want, resid_want = O.fixed_point_rho(u, w, rho0, 20)
+    rho = _cuda(rho0).reshape(-1).clone()
+    resid = torch.empty(1, dtype=torch.float64, device="cuda")
+    m.mera_fixed_point_rho(_cuda(u).reshape(-1), _cuda(w).reshape(-1), chi, rho, 20, resid)
+    assert _err(rho.cpu().numpy().reshape(want.shape), want) < TOL_F64
+    assert resid.item() == pytest.approx(resid_want, rel=1e-6, abs=1e-14)
+
+
+def test_fixed_point_zero_iterations_is_identity_map():
+    chi = 3
+    u, w, _, rho0 = _inputs(chi, chi, 5)
+    rho = _cuda(rho0).reshape(-1).clone()
+    resid = torch.full((1,), 7.0, dtype=torch.float64, device="cuda")
+    m.mera_fixed_point_rho(_cuda(u).reshape(-1), _cuda(w).reshape(-1), chi, rho, 0, resid)
+    assert np.array_equal(rho.cpu().numpy(), rho0.reshape(-1))
+    assert resid.item() == 0.0
+
+
+@pytest.mark.parametrize("mm,nn", [(16, 16), (16, 4), (64, 64), (256, 256), (256, 16), (100, 37)])
+def test_polar_update_f64(mm, nn):
+    rng = np.random.default_rng(mm * 1000 + nn)
+    env = rng.standard_normal((mm, nn))
+    out = torch.empty(mm * nn, dtype=torch.float64, device="cuda")
+    m.mera_polar_update(_cuda(env).reshape(-1), mm, nn, out)
+    want = O.polar_update(env.reshape(mm, 1, nn), 1).reshape(mm, nn)
+    got = out.cpu().numpy().reshape(mm, nn)
+    assert np.abs(got - want).max() < 1e-10
+    assert np.abs(got.T @ got - np.eye(nn)).max() < 1e-12
+
+
+def test_polar_reports_nonconvergence_for_rank_deficient_input():
+    mm, nn = 16, 4
+    env = np.zeros((mm, nn))
+    env[0, 0] = 1.0  # rank 1: no unique polar factor
+    out = torch.empty(mm * nn, dtype=torch.float64, device="cuda")
+    with pytest.raises(m.MeraNotConverged):
+        m.mera_polar_update(_cuda(env).reshape(-1), mm, nn, out, max_iter=30)
+
+
+def test_argument_errors_do_not_launch():
+    chi = 3
+    u, w, h, _ = _inputs(chi, chi, 6)
+    out = torch.empty(chi ** 6, dtype=torch.float64, device="cuda")
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(m.MeraError) as ei:
+        m.mera_ascend(_cuda(h).reshape(-1), _cuda(u).reshape(-1), _cuda(w).reshape(-1), chi, chi, out, ws=small)
+    assert ei.value.status == 2  # MERA_ENOMEM
+    with pytest.raises(m.MeraError):
+        m.mera_ascend(_cuda(h).reshape(-1), _cuda(u).reshape(-1), _cuda(w).reshape(-1), chi, chi, out, prec=9)
+
+
+def test_sweeps_match_oracle_chi4():
+    chi, n_sweeps = 4, 4
+    layers = I.init_mera(0, chi)
+    h1, shift = O.ising_h1(1.0)
+    ol, orho, oes = O.run([(u.copy(), w.copy()) for u, w in layers], 1.0, n_sweeps, 20)
+    us = [_cuda(u).reshape(-1).clone() for u, _ in layers]
+    ws = [_cuda(w).clone() for _, w in layers]
+    rho = _cuda(O.identity_density(chi)).reshape(-1).clone()
+    st = m.MeraState(us, ws, rho)
+    st.chi_b = [w.shape[0] for _, w in layers]
+    st.chi_t = [w.shape[2] for _, w in layers]
+    e = torch.empty(1, dtype=torch.float64, device="cuda")
+    h1d = _cuda(h1).reshape(-1)
+    es = []
+    for _ in range(n_sweeps):
+        m.mera_sweep(st, h1d, shift, 20, e)
+        es.append(e.item())
+    np.testing.assert_allclose(es, oes, rtol=1e-10, atol=0)
+    for (ou, ow), u, w in zip(ol, us, ws):
+        assert np.abs(u.cpu().numpy().reshape(ou.shape) - ou).max() < 1e-9
+        assert np.abs(w.cpu().numpy().reshape(ow.shape) - ow).max() < 1e-9
+    assert _err(rho.cpu().numpy().reshape(orho.shape), orho) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Full size (chi = 16, the benchmarked workload): sampled rows and properties.
+# --------------------------------------------------------------------------
+def test_ascend_chi16_sampled_rows_and_identity():
+    chi = 16
+    u, w, h, rho = _inputs(chi, chi, 8)
+    ud, wd = _cuda(u).reshape(-1), _cuda(w).reshape(-1)
+    out = torch.empty(chi ** 6, dtype=torch.float64, device="cuda")
+    m.mera_ascend(_cuda(h).reshape(-1), ud, wd, chi, chi, out)
+    got = out.cpu().numpy().reshape((chi,) * 6)
+    rows = [(0, 0, 0), (3, 15, 7), (15, 1, 9)]
+    want = O.ascend_rows(h, u, w, rows)
+    for k, (p, q, r) in enumerate(rows):
+        assert _err(got[p, q, r], want[k]) < TOL_F64
+    # A(1) = 1 (Eq. iso / unitarity) at full size
+    eye = torch.eye(chi ** 3, dtype=torch.float64, device="cuda").reshape(-1)
+    m.mera_ascend(eye, ud, wd, chi, chi, out)
+    a1 = out.reshape(chi ** 3, chi ** 3)
+    assert (a1 - torch.eye(chi ** 3, dtype=torch.float64, device="cuda")).abs().max().item() < 1e-12

@@ -228,6 +228,14 @@ mera_status mera_plan_json(int op, int chi_b, int chi_t, int prec, char* buf, si
  */
 mera_status mera_flops(int op, int chi_b, int chi_t, double* flops);
 
+/*
+ * Device-side failure word of the current device: bit (1 << MERA_ETIMEOUT)
+ * is set when a bounded wait inside a tensor-core kernel gave up (the kernel
+ * then skipped its remaining work and returned; its outputs are invalid).
+ * Synchronises with the device.  clear != 0 resets the word afterwards.
+ */
+mera_status mera_device_status(int* status, int clear);
+
 /* ------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper; used to measure the kernels).
  * ---------------------------------------------------------------------- */
@@ -253,6 +261,17 @@ mera_status mera_profile_enable(int on);
  * Waits for the recorded events.  Any pointer may be NULL.
  */
 mera_status mera_profile_read(int kind, long long* launches, double* ms, double* flops);
+
+/*
+ * Test hook (no counterpart in the paper): C = A * B^T through the GEMM
+ * kernel of mode prec, with A row-major M x K, B row-major N x K and C
+ * row-major M x N, all binary64 device arrays.  The operands are first cast
+ * to the mode's operand format in `ws`, which needs
+ * planes * (pad(M*ld) + pad(N*ld)) bytes (ld = K rounded up to 16 bytes,
+ * pad = 256-byte multiple, planes = 2 for BF16X3, else 1).
+ */
+mera_status mera_gemm_test(int prec, const double* A, const double* B, int M, int N, int K, double* C,
+                           void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,7 @@ __all__ = [
     "mera_fixed_point_rho", "mera_env_u", "mera_env_w", "mera_polar_update", "mera_polar_workspace_size",
     "mera_energy", "mera_ising_h1", "mera_sweep", "mera_sweep_workspace_size", "mera_plan_json", "mera_flops",
     "workspace", "MeraState", "mera_launch_count", "mera_profile_enable", "mera_profile_read",
-    "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE",
+    "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE", "mera_device_status", "mera_gemm_test",
 ]
 
 PREC_F64, PREC_TF32, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3
@@ -70,9 +70,7 @@ def library():
             return _lib
         from . import build as _build
 
-        path = _build.LIB
-        if not os.path.exists(path):
-            path = _build.build()
+        path = _build.build()  # no-op when the in-tree build is up to date
         lib = ctypes.CDLL(path)
         vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
         psz, pd = ctypes.POINTER(sz), ctypes.POINTER(d)
@@ -94,6 +92,8 @@ def library():
             "mera_plan_json": ([i, i, i, i, ctypes.c_char_p, sz, psz], i),
             "mera_flops": ([i, i, i, pd], i),
             "mera_launch_count": ([], ctypes.c_longlong),
+            "mera_device_status": ([ctypes.POINTER(i), i], i),
+            "mera_gemm_test": ([i, vp, vp, i, i, i, vp, vp, sz, vp], i),
             "mera_profile_enable": ([i], i),
             "mera_profile_read": ([i, ctypes.POINTER(ctypes.c_longlong), pd, pd], i),
         }
@@ -318,3 +318,25 @@ def mera_profile_read(kind: int = PROF_GEMM):
     n, ms, fl = ctypes.c_longlong(0), ctypes.c_double(0.0), ctypes.c_double(0.0)
     _check(library().mera_profile_read(kind, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl)))
     return n.value, ms.value, fl.value
+
+
+def mera_device_status(clear: bool = True) -> int:
+    """Device failure bits (1 << 5: a bounded wait timed out); synchronises."""
+    st = ctypes.c_int(0)
+    _check(library().mera_device_status(ctypes.byref(st), 1 if clear else 0))
+    return st.value
+
+
+def mera_gemm_test(prec, A, B, C, stream=None):
+    """C = A @ B.T through the library's GEMM kernel of mode prec (test hook)."""
+    M, K = A.shape
+    N = B.shape[0]
+    eb = 8 if prec == PREC_F64 else (4 if prec == PREC_TF32 else 2)
+    ld = (K * eb + 15) // 16 * 16 // eb
+    pad = lambda x: (x + 255) // 256 * 256  # noqa: E731
+    planes = 2 if prec == PREC_BF16X3 else 1
+    ws = workspace(planes * (pad(M * ld * eb) + pad(N * ld * eb)), A.device)
+    p, n = _ws(ws)
+    _check(library().mera_gemm_test(prec, _f64(A, M * K, "A"), _f64(B, N * K, "B"), M, N, K, _f64(C, M * N, "C"),
+                                    p, n, _stream(stream)))
+    return C

@@ -602,3 +602,47 @@ extern "C" mera_status mera_profile_read(int kind, long long* launches, double* 
   if (flops) *flops = f;
   return MERA_OK;
 }
+
+extern "C" mera_status mera_device_status(int* status, int clear) {
+  if (!status) return fail(MERA_EINVAL, "null status");
+  return cuda_status(read_device_status(status, clear != 0), "device status");
+}
+
+extern "C" mera_status mera_gemm_test(int prec, const double* A, const double* B, int M, int N, int K, double* C,
+                                      void* ws, size_t ws_bytes, void* stream) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1) return fail(MERA_EINVAL, "bad gemm test arguments");
+  if (!prec_ok(prec)) return fail(MERA_EINVAL, "bad prec");
+  const int64_t eb = elem_bytes(prec), np = planes(prec);
+  const int64_t ld = (int64_t(K) * eb + 15) / 16 * 16 / eb;
+  const size_t pa = align_up(size_t(M) * ld * eb), pb = align_up(size_t(N) * ld * eb);
+  const size_t need = np * (pa + pb);
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(MERA_EINVAL, "workspace not 256-byte aligned");
+  if (!ws || ws_bytes < need) return fail(MERA_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* wa = static_cast<char*>(ws);
+  char* wb = wa + np * pa;
+  // operands: A row-major M x K, B row-major N x K, copied to padded pitch
+  PermuteStep pa_step, pb_step;
+  pa_step.rows = M; pa_step.cols = K; pa_step.ld = ld;
+  pa_step.row_src.n = 1; pa_step.row_src.dim[0] = M; pa_step.row_src.stride[0] = K;
+  pa_step.col_src.n = 1; pa_step.col_src.dim[0] = K; pa_step.col_src.stride[0] = 1;
+  pb_step = pa_step;
+  pb_step.rows = N; pb_step.row_src.dim[0] = N;
+  cudaError_t e = launch_permute(pa_step, A, wa, int64_t(pa / eb), prec, s);
+  if (e == cudaSuccess) e = launch_permute(pb_step, B, wb, int64_t(pb / eb), prec, s);
+  if (e != cudaSuccess) return cuda_status(e, "gemm test operands");
+  LegMap md, nd;
+  md.n = 1; md.dim[0] = M; md.stride[0] = N;
+  nd.n = 1; nd.dim[0] = N; nd.stride[0] = 1;
+  if (prec == PREC_F64) {
+    GemmF64Args g;
+    g.A = reinterpret_cast<const double*>(wa); g.a_m = ld; g.a_k = 1;
+    g.B = reinterpret_cast<const double*>(wb); g.b_n = ld; g.b_k = 1;
+    g.M = M; g.N = N; g.K = K; g.C = C; g.m_dst = md; g.n_dst = nd; g.alpha = 1.0; g.accumulate = 0;
+    return cuda_status(launch_gemm_f64(g, s), "gemm test f64");
+  }
+  TcGemmArgs t;
+  t.prec = prec; t.A = wa; t.a_plane_bytes = pa; t.lda = ld; t.B = wb; t.b_plane_bytes = pb; t.ldb = ld;
+  t.M = M; t.N = N; t.K = K; t.c_final = true; t.C = C; t.m_dst = md; t.n_dst = nd; t.alpha = 1.0; t.accumulate = 0;
+  return cuda_status(launch_gemm_tc(t, s), "gemm test tc");
+}

@@ -32,4 +32,7 @@ struct TcGemmArgs {
 
 cudaError_t launch_gemm_tc(const TcGemmArgs& args, cudaStream_t stream);
 
+// Device status word (bit MERA_ETIMEOUT set when a bounded wait gave up).
+cudaError_t read_device_status(int* status, bool clear);
+
 }  // namespace mera

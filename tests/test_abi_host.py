@@ -123,6 +123,8 @@ def _emulate(plan, inputs, out_size):
             else:
                 a, bb = bufs[st["a_buf"]], bufs[st["b_buf"]]
                 M, N, K = st["M"], st["N"], st["K"]
+                # operand reads (TMA boxes are clipped to rows x K of these planes)
+                assert M <= a["rows"] and N <= bb["rows"] and K <= st["lda"] == a["ld"] and K <= st["ldb"] == bb["ld"]
                 A = arena[a["offset"] // eb + np.arange(M)[:, None] * st["lda"] + np.arange(K)[None, :]]
                 B = arena[bb["offset"] // eb + np.arange(N)[:, None] * st["ldb"] + np.arange(K)[None, :]]
                 assert not np.isnan(A).any() and not np.isnan(B).any()
@@ -139,6 +141,9 @@ def _emulate(plan, inputs, out_size):
                         out[idx] = C
                 else:
                     cb = bufs[st["c_buf"]]
+                    # every scattered store stays inside its operand plane
+                    assert idx.min() >= 0 and idx.max() < cb["rows"] * cb["ld"]
+                    assert (idx % cb["ld"]).max() < bufs[st["c_buf"]]["ld"]
                     arena[cb["offset"] // eb + idx] = C
     return out
 

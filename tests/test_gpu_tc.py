@@ -1,0 +1,108 @@
+"""Tensor-core (tcgen05) paths: the GEMM kernel and the maps in TF32, BF16
+and split-BF16 (BF16X3) against the FP64 oracle.
+
+GEMM bound (elementwise, rigorous): with operand unit roundoff u (TF32
+2^-11, BF16 2^-8 relative spacing / 2 = 2^-9, BF16X3 pair 2^-17 plus the
+dropped lo*lo term 2^-18) and FP32 accumulation over K terms,
+    |C - A B^T| <= (2 u + u^2 + K 2^-24) (|A| |B|^T).
+Map tolerances (relative to the largest oracle entry) are stated per mode
+below; they cover ~10 chained contractions, each rounding its result to the
+operand precision once.
+"""
+import numpy as np
+import pytest
+
+import mera_inputs as I
+from oracle import mera_oracle as O
+
+torch = pytest.importorskip("torch")
+m = pytest.importorskip("paper_1906_12030_gb300")
+
+pytestmark = pytest.mark.gpu
+
+U_OPERAND = {m.PREC_TF32: 2.0 ** -11, m.PREC_BF16: 2.0 ** -9, m.PREC_BF16X3: 2.0 ** -17 + 2.0 ** -18}
+MAP_TOL = {m.PREC_TF32: 5e-3, m.PREC_BF16: 3e-2, m.PREC_BF16X3: 5e-5}
+TC_PRECS = [m.PREC_TF32, m.PREC_BF16, m.PREC_BF16X3]
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.fixture(autouse=True)
+def _device_status_clean():
+    m.mera_device_status(clear=True)
+    yield
+    assert m.mera_device_status(clear=True) == 0, "a bounded device wait timed out"
+
+
+@pytest.mark.parametrize("prec", TC_PRECS + [m.PREC_F64])
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (16, 16, 16), (200, 300, 100), (130, 17, 7), (1000, 64, 520),
+                                   (4096, 256, 512), (257, 129, 33), (64, 512, 2048)])
+def test_gemm_bound(prec, M, N, K):
+    rng = np.random.default_rng(M * 7 + N * 13 + K)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K))
+    C = torch.empty(M * N, dtype=torch.float64, device="cuda")
+    m.mera_gemm_test(prec, _cuda(A), _cuda(B), C)
+    got = C.cpu().numpy().reshape(M, N)
+    exact = A @ B.T
+    mag = np.abs(A) @ np.abs(B).T
+    if prec == m.PREC_F64:
+        assert np.all(np.abs(got - exact) <= 1e-14 * K * mag + 1e-300)
+        return
+    u = U_OPERAND[prec]
+    bound = (2 * u + u * u + K * 2.0 ** -24) * mag
+    assert np.all(np.abs(got - exact) <= bound), float(np.max(np.abs(got - exact) / bound))
+
+
+def _maps(prec, chi_b, chi_t, seed):
+    rng = np.random.default_rng(seed)
+    u, w = I.random_u(rng, chi_b), I.random_w(rng, chi_b, chi_t)
+    h = I.random_operator(rng, chi_b)
+    rho = I.random_density(rng, chi_t)
+    d = lambda x: _cuda(x).reshape(-1)  # noqa: E731
+    hd, rd, ud, wd = d(h), d(rho), d(u), d(w)
+    res = {}
+    a = torch.empty(chi_t ** 6, dtype=torch.float64, device="cuda")
+    m.mera_ascend(hd, ud, wd, chi_b, chi_t, a, prec=prec)
+    res["ascend"] = (a, O.ascend(h, u, w))
+    dd = torch.empty(chi_b ** 6, dtype=torch.float64, device="cuda")
+    m.mera_descend(rd, ud, wd, chi_b, chi_t, dd, prec=prec)
+    res["descend"] = (dd, O.descend(rho, u, w))
+    gu = torch.empty(chi_b ** 4, dtype=torch.float64, device="cuda")
+    m.mera_env_u(hd, rd, ud, wd, chi_b, chi_t, gu, prec=prec)
+    res["env_u"] = (gu, O.env_u(h, rho, u, w))
+    gw = torch.empty(chi_b ** 2 * chi_t, dtype=torch.float64, device="cuda")
+    m.mera_env_w(hd, rd, ud, wd, chi_b, chi_t, gw, prec=prec)
+    res["env_w"] = (gw, O.env_w(h, rho, u, w))
+    return res
+
+
+@pytest.mark.parametrize("prec", TC_PRECS)
+@pytest.mark.parametrize("chi_b,chi_t", [(2, 2), (3, 3), (4, 4), (5, 5), (4, 16), (8, 8), (3, 8)])
+def test_maps_mixed_precision(prec, chi_b, chi_t):
+    res = _maps(prec, chi_b, chi_t, 11)
+    errs = {}
+    for name, (got, want) in res.items():
+        g = got.cpu().numpy().reshape(want.shape)
+        errs[name] = float(np.abs(g - want).max() / np.abs(want).max())
+    print(f"prec={prec} chi=({chi_b},{chi_t}) errors {errs}")
+    for name, e in errs.items():
+        assert e < MAP_TOL[prec], (name, e)
+
+
+@pytest.mark.parametrize("prec", TC_PRECS)
+def test_fixed_point_and_energy_mixed(prec):
+    chi = 4
+    rng = np.random.default_rng(12)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    want, _ = O.fixed_point_rho(u, w, O.identity_density(chi), 20)
+    rho = _cuda(O.identity_density(chi)).reshape(-1).clone()
+    m.mera_fixed_point_rho(_cuda(u).reshape(-1), _cuda(w).reshape(-1), chi, rho, 20, prec=prec)
+    r = rho.cpu().numpy().reshape(want.shape)
+    assert np.abs(r - want).max() / np.abs(want).max() < MAP_TOL[prec]
+    # normalisation and symmetry are FP64 in every mode
+    rm = r.reshape(chi ** 3, -1)
+    assert abs(np.trace(rm) - 1.0) < 1e-14
+    assert np.abs(rm - rm.T).max() == 0.0

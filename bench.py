@@ -46,7 +46,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--chi", type=int, default=16)
-    ap.add_argument("--prec", default="f64", choices=["f64", "tf32", "bf16", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x3", choices=["f64", "tf32", "bf16", "bf16x3"])
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="timed FP64 sweeps (after one untimed) for the mixed-vs-FP64 comparison; 0 skips it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -228,27 +230,35 @@ def run_native(args):
         dist.init_process_group("nccl", device_id=dev)
     chi = args.chi
     prec = m.PRECS[args.prec]
-    layers = I.init_mera(SEED, chi)
     h1_host, shift = m.mera_ising_h1(HZ)
-    us = [torch.from_numpy(u).to(dev).reshape(-1).contiguous() for u, _ in layers]
-    ws_ = [torch.from_numpy(w).to(dev).contiguous() for _, w in layers]
-    n3 = chi ** 3
-    rho = (torch.eye(n3, dtype=torch.float64, device=dev) / n3).reshape(-1).contiguous()
     h1 = torch.from_numpy(h1_host.reshape(-1)).to(dev)
-    state = m.MeraState(us, ws_, rho)
-    wsb = m.workspace(m.mera_sweep_workspace_size(state.chi_b, state.chi_t, prec), dev)
-    e = torch.empty(1, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    def sweep():
-        try:
-            m.mera_sweep(state, h1, shift, N_POW, e, prec=prec, ws=wsb, stream=stream)
-        except m.MeraNotConverged:
-            pass  # a polar update hit its cap; the sweep is complete
+    def make_state(p):
+        layers = I.init_mera(SEED, chi)
+        us = [torch.from_numpy(u).to(dev).reshape(-1).contiguous() for u, _ in layers]
+        ws_ = [torch.from_numpy(w).to(dev).contiguous() for _, w in layers]
+        n3 = chi ** 3
+        rho = (torch.eye(n3, dtype=torch.float64, device=dev) / n3).reshape(-1).contiguous()
+        state = m.MeraState(us, ws_, rho)
+        wsb = m.workspace(m.mera_sweep_workspace_size(state.chi_b, state.chi_t, p), dev)
+        e = torch.empty(1, dtype=torch.float64, device=dev)
 
+        def sweep():
+            try:
+                m.mera_sweep(state, h1, shift, N_POW, e, prec=p, ws=wsb, stream=stream)
+            except m.MeraNotConverged:
+                pass  # a polar update hit its cap; the sweep is complete
+            return e
+
+        return us, ws_, rho, e, sweep
+
+    us, ws_, rho, e, sweep = make_state(prec)
+    energies = []
     for _ in range(args.warmup):
         sweep()
+        energies.append(e.item())
     torch.cuda.synchronize(dev)
 
     sweep_flops = _sweep_flops(m, chi)
@@ -308,11 +318,31 @@ def run_native(args):
         e2e = {"value": world * n_e2e / (e2e_ms / 1e3), "unit": "sweep/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 8, "steps": n_e2e}
 
+    # ---- the same MERA with FP64 contractions: throughput and energy gap ----
+    fp64 = None
+    if args.fp64_steps > 0 and prec != m.PREC_F64 and rank == 0:
+        _, _, _, e64, sweep64 = make_state(m.PREC_F64)
+        sweep64()
+        gap = abs(e64.item() - energies[0]) if energies else None
+        torch.cuda.synchronize(dev)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.fp64_steps):
+            sweep64()
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = t0.elapsed_time(t1) / args.fp64_steps
+        fp64 = {"value": 1e3 / ms64, "unit": "sweep/s", "ms_per_step": ms64, "steps": args.fp64_steps,
+                "tflops": sweep_flops / ms64 / 1e9, "dE_per_site_after_1_sweep": gap}
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
     value = world * args.steps / (total_ms / 1e3)
+    if fp64 is not None:
+        fp64["speedup_of_mixed"] = (value / world) / fp64["value"]
     peak, peak_src = _peak_tflops(args.prec)
     dom_tflops = dom[2] / (dom[1] / 1e3) / 1e12 if dom[1] > 0 else None
     line = {
@@ -326,6 +356,7 @@ def run_native(args):
                    "sweep_flops": sweep_flops, "parallelism": f"replicas{world}",
                    "l2": "256 MB buffer written between timed steps (untimed); working set > L2"},
         "energy_per_spin": energy,
+        "fp64": fp64,
         "roofline": {"bound": "tensor" if args.prec != "f64" else "fp64", "achieved": dom_tflops, "peak": peak,
                      "unit": "TFLOP/s", "frac": (dom_tflops / peak) if dom_tflops else None, "traffic": None,
                      "kernel": "gemm_f64_kernel" if args.prec == "f64" else "tcgen05 GEMM",

@@ -1,13 +1,20 @@
 """Tensor-core (tcgen05) paths: the GEMM kernel and the maps in TF32, BF16
 and split-BF16 (BF16X3) against the FP64 oracle.
 
-GEMM bound (elementwise, rigorous): with operand unit roundoff u (TF32
-2^-11, BF16 2^-8 relative spacing / 2 = 2^-9, BF16X3 pair 2^-17 plus the
-dropped lo*lo term 2^-18) and FP32 accumulation over K terms,
-    |C - A B^T| <= (2 u + u^2 + K 2^-24) (|A| |B|^T).
-Map tolerances (relative to the largest oracle entry) are stated per mode
-below; they cover ~10 chained contractions, each rounding its result to the
-operand precision once.
+GEMM bound (elementwise, rigorous): with operand unit roundoff u and FP32
+accumulation over K terms,
+    |C - A B^T| <= (2 u + u^2 + K 2^-24) (|A| |B|^T),
+u = 2^-11 + 2^-24 for TF32 (11 significant bits after the binary64 -> FP32
+rounding), 2^-8 for BF16 (8 significant bits), and 1.5 * 2^-16 for the BF16
+pair: hi + lo represents x to 2^-16 |x| and the dropped lo*lo product is at
+most 2^-16 |a b|, so 2u >= 3 * 2^-16.
+Map tolerances (relative to the largest oracle entry): a diagram is ~10
+chained contractions, each rounding its result to the operand precision
+once (~10 u in a random walk, x2 for the even + odd / 4-6 hole sums) and
+accumulating up to K = chi_t^3 products in FP32.  TF32: 10 u = 5e-3.
+BF16: 10 u = 4e-2 (3e-2 kept, 3x the measured 9e-3).  BF16X3: 10 u =
+2.3e-4 plus the FP32 accumulation bound K 2^-24 = 2.4e-4 at K = 4096,
+i.e. 5e-4.
 """
 import numpy as np
 import pytest
@@ -20,8 +27,8 @@ m = pytest.importorskip("paper_1906_12030_gb300")
 
 pytestmark = pytest.mark.gpu
 
-U_OPERAND = {m.PREC_TF32: 2.0 ** -11, m.PREC_BF16: 2.0 ** -9, m.PREC_BF16X3: 2.0 ** -17 + 2.0 ** -18}
-MAP_TOL = {m.PREC_TF32: 5e-3, m.PREC_BF16: 3e-2, m.PREC_BF16X3: 5e-5}
+U_OPERAND = {m.PREC_TF32: 2.0 ** -11 + 2.0 ** -24, m.PREC_BF16: 2.0 ** -8, m.PREC_BF16X3: 1.5 * 2.0 ** -16}
+MAP_TOL = {m.PREC_TF32: 5e-3, m.PREC_BF16: 3e-2, m.PREC_BF16X3: 5e-4}
 TC_PRECS = [m.PREC_TF32, m.PREC_BF16, m.PREC_BF16X3]
 
 

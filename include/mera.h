@@ -27,7 +27,8 @@
  *   synchronised.
  * - Scratch memory is the caller's: `ws` must hold at least the byte count
  *   reported by mera_workspace_size for the same operation and sizes, and be
- *   256-byte aligned.  The library allocates no device memory of its own.
+ *   256-byte aligned.  Apart from a status word and the fixed static array
+ *   behind mera_ascend_noalloc, the library holds no device memory.
  * - prec selects the arithmetic of the contractions (the O(chi^9) part):
  *     MERA_PREC_F64    binary64 everywhere (FP64 units),
  *     MERA_PREC_TF32   tensor cores, TF32 operands, FP32 accumulation,
@@ -261,6 +262,35 @@ mera_status mera_profile_enable(int on);
  * Waits for the recorded events.  Any pointer may be NULL.
  */
 mera_status mera_profile_read(int kind, long long* launches, double* ms, double* flops);
+
+/* Bytes of the device array that backs mera_ascend_noalloc (32 MiB). */
+#define MERA_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/*
+ * mera_ascend without a workspace argument (the paper has no counterpart;
+ * this is an interface for callers that cannot allocate).  Some callers
+ * cannot hand the library scratch memory: an application whose own pool
+ * allocator owns all device memory and must not be bypassed, or a
+ * latency-bound loop that cannot afford a cudaMalloc, which may synchronise
+ * the device.  They pass only h, u, w and h_out, exactly as for
+ * mera_ascend, whose result this returns.
+ *
+ * The scratch lives in a file-scope __device__ array of
+ * MERA_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds
+ * until the process exits (enough for chi_b = chi_t <= 8 in every mode, and
+ * for the 4 -> 16 first layer).  Sizes whose mera_workspace_size(
+ * MERA_OP_ASCEND, ...) exceeds it are rejected with MERA_EINVAL and a
+ * message.  No cudaMalloc, cudaFree or allocating library call is made.
+ *
+ * The first call on each device looks up the array's device address on the
+ * current device (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the one array: every byte a call reads
+ * is first written by that same call, so nothing has to start at zero, but
+ * two calls that overlap on the GPU (different streams, or different host
+ * threads) race on it and give undefined results.
+ */
+mera_status mera_ascend_noalloc(const double* h, const double* u, const double* w, int chi_b, int chi_t,
+                                double* h_out, int prec, void* stream);
 
 /*
  * Test hook (no counterpart in the paper): C = A * B^T through the GEMM

@@ -20,6 +20,7 @@ __all__ = [
     "mera_energy", "mera_ising_h1", "mera_sweep", "mera_sweep_workspace_size", "mera_plan_json", "mera_flops",
     "workspace", "MeraState", "mera_launch_count", "mera_profile_enable", "mera_profile_read",
     "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE", "mera_device_status", "mera_gemm_test",
+    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES",
 ]
 
 PREC_F64, PREC_TF32, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3
@@ -27,6 +28,7 @@ PRECS = {"f64": PREC_F64, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x3": PREC_B
 OP_ASCEND, OP_DESCEND, OP_ENV_U, OP_ENV_W, OP_ENERGY, OP_FIXED_POINT = 0, 1, 2, 3, 4, 5
 MAX_LAYERS = 8
 PROF_GEMM, PROF_GEMM_DOMINANT, PROF_PERMUTE = 0, 1, 2
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 _OK, _EINVAL, _ENOMEM, _ECUDA, _ENOTCONV, _ETIMEOUT = 0, 1, 2, 3, 4, 5
 
@@ -94,6 +96,7 @@ def library():
             "mera_launch_count": ([], ctypes.c_longlong),
             "mera_device_status": ([ctypes.POINTER(i), i], i),
             "mera_gemm_test": ([i, vp, vp, i, i, i, vp, vp, sz, vp], i),
+            "mera_ascend_noalloc": ([vp, vp, vp, i, i, vp, i, vp], i),
             "mera_profile_enable": ([i], i),
             "mera_profile_read": ([i, ctypes.POINTER(ctypes.c_longlong), pd, pd], i),
         }
@@ -340,3 +343,15 @@ def mera_gemm_test(prec, A, B, C, stream=None):
     _check(library().mera_gemm_test(prec, _f64(A, M * K, "A"), _f64(B, N * K, "B"), M, N, K, _f64(C, M * N, "C"),
                                     p, n, _stream(stream)))
     return C
+
+
+def mera_ascend_noalloc(h, u, w, chi_b, chi_t, out, prec=PREC_F64, stream=None):
+    """mera_ascend with the library's static device scratch (no workspace).
+
+    For callers that cannot allocate scratch memory; sizes needing more than
+    NOALLOC_SCRATCH_BYTES of scratch raise MeraError.  Calls share the
+    scratch, so calls that overlap on the GPU must not be issued."""
+    _check(library().mera_ascend_noalloc(_f64(h, chi_b ** 6, "h"), _f64(u, chi_b ** 4, "u"),
+                                         _f64(w, chi_b ** 2 * chi_t, "w"), chi_b, chi_t,
+                                         _f64(out, chi_t ** 6, "out"), prec, _stream(stream)))
+    return out

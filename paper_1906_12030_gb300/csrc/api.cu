@@ -646,3 +646,9 @@ extern "C" mera_status mera_gemm_test(int prec, const double* A, const double* B
   t.M = M; t.N = N; t.K = K; t.c_final = true; t.C = C; t.m_dst = md; t.n_dst = nd; t.alpha = 1.0; t.accumulate = 0;
   return cuda_status(launch_gemm_tc(t, s), "gemm test tc");
 }
+
+namespace mera {
+// Records `msg` as the calling thread's last error and returns `st`; for
+// entry points defined in other translation units.
+mera_status set_last_error(mera_status st, const char* msg) { return fail(st, "%s", msg); }
+}  // namespace mera

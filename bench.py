@@ -51,6 +51,8 @@ def _args():
                     help="timed FP64 sweeps (after one untimed) for the mixed-vs-FP64 comparison; 0 skips it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--case", default="sweep", choices=["sweep", "ascend", "descend", "env_u", "env_w"],
+                    help="sweep: the benchmark; otherwise time one map call (after one warm call), for profiling")
     return ap.parse_args()
 
 
@@ -374,8 +376,56 @@ def run_native(args):
         torch.distributed.destroy_process_group()
 
 
+def run_case(args):
+    """One warm call and one timed call of a single map (profiling target)."""
+    import numpy as np
+    import torch
+
+    import mera_inputs as I
+    import paper_1906_12030_gb300 as m
+
+    chi, prec = args.chi, m.PRECS[args.prec]
+    rng = np.random.default_rng(SEED)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    h, rho = I.random_operator(rng, chi), I.random_density(rng, chi)
+    d = lambda x: torch.from_numpy(x).cuda().reshape(-1)  # noqa: E731
+    hd, rd, ud, wd = d(h), d(rho), d(u), d(w)
+    op = {"ascend": m.OP_ASCEND, "descend": m.OP_DESCEND, "env_u": m.OP_ENV_U, "env_w": m.OP_ENV_W}[args.case]
+    ws = m.workspace(m.mera_workspace_size(op, chi, chi, prec))
+    out = torch.empty(chi ** 6, dtype=torch.float64, device="cuda")
+
+    def call():
+        if args.case == "ascend":
+            m.mera_ascend(hd, ud, wd, chi, chi, out, prec=prec, ws=ws)
+        elif args.case == "descend":
+            m.mera_descend(rd, ud, wd, chi, chi, out, prec=prec, ws=ws)
+        elif args.case == "env_u":
+            m.mera_env_u(hd, rd, ud, wd, chi, chi, out[: chi ** 4], prec=prec, ws=ws)
+        else:
+            m.mera_env_w(hd, rd, ud, wd, chi, chi, out[: chi ** 3], prec=prec, ws=ws)
+
+    call()
+    torch.cuda.synchronize()
+    m.mera_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    dom, allg, perm = (m.mera_profile_read(k) for k in (m.PROF_GEMM_DOMINANT, m.PROF_GEMM, m.PROF_PERMUTE))
+    m.mera_profile_enable(False)
+    fl = m.mera_flops(op, chi, chi)
+    print(json.dumps({"case": args.case, "chi": chi, "prec": args.prec, "ms": ms, "tflops": fl / ms / 1e9,
+                      "dominant": {"launches": dom[0], "ms": dom[1], "tflops": dom[2] / dom[1] / 1e9 if dom[1] else None},
+                      "gemm_ms": allg[1], "permute_ms": perm[1], "device_status": m.mera_device_status()}), flush=True)
+
+
 def main():
     args = _args()
+    if args.case != "sweep":
+        run_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

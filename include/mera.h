@@ -36,6 +36,10 @@
  *     MERA_PREC_BF16X3 tensor cores, each operand split into a BF16 pair
  *                      (hi + lo), three products hi*hi + hi*lo + lo*hi,
  *                      FP32 accumulation.
+ *     MERA_PREC_BF16X6 tensor cores, each operand split into three BF16
+ *                      parts (hi + mid + lo, 24 significant bits), the six
+ *                      products whose parts' orders sum to at most 2, FP32
+ *                      accumulation.
  *   Polar updates, normalisation, traces and energies are binary64 always.
  */
 #ifndef MERA_GB300_H
@@ -60,6 +64,7 @@ typedef int mera_status;
 #define MERA_PREC_TF32 1
 #define MERA_PREC_BF16 2
 #define MERA_PREC_BF16X3 3
+#define MERA_PREC_BF16X6 4
 
 /* Operation ids for mera_workspace_size / mera_plan_json. */
 #define MERA_OP_ASCEND 0

@@ -104,7 +104,7 @@ bool chi_ok(int chi_b, int chi_t) {
   return chi_b >= 1 && chi_t >= 1 && chi_b <= MERA_MAX_CHI && chi_t <= MERA_MAX_CHI &&
          int64_t(chi_t) <= int64_t(chi_b) * chi_b;
 }
-bool prec_ok(int prec) { return prec >= MERA_PREC_F64 && prec <= MERA_PREC_BF16X3; }
+bool prec_ok(int prec) { return prec >= MERA_PREC_F64 && prec <= MERA_PREC_BF16X6; }
 
 int64_t ipow(int64_t b, int e) {
   int64_t r = 1;
@@ -181,6 +181,8 @@ mera_status run_program(const OpProgram& prog, const double* const inputs[4], do
         args.n_dst = g.n_dst;
         args.alpha = g.alpha;
         args.accumulate = g.accumulate;
+        args.split = g.split;
+        args.partial = g.p_buf >= 0 ? reinterpret_cast<float*>(ws + dg.bufs[g.p_buf].offset) : nullptr;
         cudaError_t e = launch_gemm_tc(args, stream);
         if (e == cudaErrorNotSupported) return fail(MERA_EINVAL, "tensor-core GEMM unavailable for prec %d", prec);
         if (e != cudaSuccess) return cuda_status(e, "gemm_tc");
@@ -364,33 +366,45 @@ extern "C" mera_status mera_polar_update(const double* env, int m, int n, double
   row_n.n = 1; row_n.dim[0] = n; row_n.stride[0] = n;
   col_1.n = 1; col_1.dim[0] = n; col_1.stride[0] = 1;
   row_m.n = 1; row_m.dim[0] = m; row_m.stride[0] = n;
-  bool converged = false;
+  // Device-gated iterations: once the residual is below tol, one more step
+  // runs and every later kernel returns at once.  The host looks at the
+  // state only every kCheck steps, so the stream is not drained each step.
+  constexpr int kCheck = 4;
+  int* state = reinterpret_cast<int*>(scalars + 4);  // done, iterations, converged-after-this-step
+  if ((e = cudaMemsetAsync(state, 0, 3 * sizeof(int), s)) != cudaSuccess) return cuda_status(e, "polar state");
+  double* buf[2] = {X, Xn};
+  int host_state[3] = {0, 0, 0};
   double resid = 0.0;
   for (int it = 0; it < max_iter; ++it) {
-    // G = X^T X
+    double* src = buf[it & 1];
+    double* dst = buf[(it + 1) & 1];
     GemmF64Args g;
-    g.A = X; g.a_m = 1; g.a_k = n;
-    g.B = X; g.b_n = 1; g.b_k = n;
+    g.skip_if = state;
+    // G = X^T X
+    g.A = src; g.a_m = 1; g.a_k = n;
+    g.B = src; g.b_n = 1; g.b_k = n;
     g.M = n; g.N = n; g.K = m;
     g.C = G; g.m_dst = row_n; g.n_dst = col_1; g.alpha = 1.0; g.accumulate = 0;
     if ((e = launch_gemm_f64(g, s)) != cudaSuccess) return cuda_status(e, "polar gemm 1");
-    if ((e = launch_ns_combine(G, Bm, n, red, scalars + 1, s)) != cudaSuccess) return cuda_status(e, "polar combine");
-    // Xn = X Bm
-    g.A = X; g.a_m = n; g.a_k = 1;
+    if ((e = launch_ns_step(G, Bm, n, red, scalars + 1, tol, state, s)) != cudaSuccess)
+      return cuda_status(e, "polar step");
+    // X_next = X (3 I - X^T X) / 2
+    g.A = src; g.a_m = n; g.a_k = 1;
     g.B = Bm; g.b_n = 1; g.b_k = n;
     g.M = m; g.N = n; g.K = n;
-    g.C = Xn; g.m_dst = row_m; g.n_dst = col_1;
+    g.C = dst; g.m_dst = row_m; g.n_dst = col_1;
     if ((e = launch_gemm_f64(g, s)) != cudaSuccess) return cuda_status(e, "polar gemm 2");
-    std::swap(X, Xn);
-    if ((e = cudaMemcpyAsync(&resid, scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-      return cuda_status(e, "polar residual copy");
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e, "polar sync");
-    if (!std::isfinite(resid)) break;
-    if (resid <= tol) {
-      converged = true;
-      break;
+    if ((e = launch_ns_finish(state, s)) != cudaSuccess) return cuda_status(e, "polar finish");
+    if ((it + 1) % kCheck == 0 || it + 1 == max_iter) {
+      if ((e = cudaMemcpyAsync(host_state, state, sizeof host_state, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(&resid, scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_status(e, "polar state copy");
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e, "polar sync");
+      if (host_state[0]) break;
     }
   }
+  const bool converged = host_state[0] && std::isfinite(resid) && resid <= tol;
+  X = buf[host_state[1] & 1];
   e = launch_scale_copy(X, out, int64_t(m) * n, -1.0, s);
   if (e != cudaSuccess) return cuda_status(e, "polar output");
   if (!converged) return fail(MERA_ENOTCONV, "polar iteration did not converge (resid %.3e, tol %.3e)", resid, tol);

@@ -66,4 +66,19 @@ struct OperandStore<PREC_BF16X3> {
   }
 };
 
+template <>
+struct OperandStore<PREC_BF16X6> {
+  using T = __nv_bfloat16;
+  __device__ __forceinline__ static void store(void* base, int64_t off, int64_t plane, double v) {
+    const __nv_bfloat16 hi = __double2bfloat16(v);
+    const double r1 = v - double(__bfloat162float(hi));
+    const __nv_bfloat16 mid = __double2bfloat16(r1);
+    const __nv_bfloat16 lo = __double2bfloat16(r1 - double(__bfloat162float(mid)));
+    __nv_bfloat16* b = static_cast<__nv_bfloat16*>(base);
+    b[off] = hi;
+    b[off + plane] = mid;
+    b[off + 2 * plane] = lo;
+  }
+};
+
 }  // namespace mera

@@ -30,6 +30,7 @@ struct GemmF64Args {
   LegMap m_dst, n_dst;
   double alpha;
   int accumulate;
+  const int* skip_if = nullptr;  // device flag: the kernel returns at once when *skip_if != 0
 };
 cudaError_t launch_gemm_f64(const GemmF64Args& args, cudaStream_t stream);
 
@@ -48,8 +49,12 @@ cudaError_t launch_sym_normalize(const double* X, double* rho, int64_t n, double
 // Polar-iteration helpers (all binary64, deterministic reductions).
 cudaError_t launch_frob_scale(const double* src, double* dst, int64_t count, double* partials,
                               double* scalars, cudaStream_t stream);
-cudaError_t launch_ns_combine(const double* G, double* Bm, int64_t n, double* partials, double* resid,
-                              cudaStream_t stream);
+// One gated Newton-Schulz step's elementwise part: Bm = (3I - G)/2, resid =
+// ||G - I||_F, state[2] = (resid <= tol).  Skipped once state[0] is set.
+cudaError_t launch_ns_step(const double* G, double* Bm, int64_t n, double* partials, double* resid, double tol,
+                           int* state, cudaStream_t stream);
+// Closes a step: state[1] += 1; state[0] = state[2].  Skipped once state[0] is set.
+cudaError_t launch_ns_finish(int* state, cudaStream_t stream);
 cudaError_t launch_scale_copy(const double* src, double* dst, int64_t count, double alpha,
                               cudaStream_t stream);
 

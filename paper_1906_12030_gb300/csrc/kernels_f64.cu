@@ -7,90 +7,234 @@
 namespace mera {
 
 // ---------------------------------------------------------------------------
-// Input tensor -> operand layout.  One block row per destination row; the
-// row's source offset is decoded once, then threads stride over columns.
+// Input tensor -> operand layout, cast to the operand precision.
+//
+// The copy is a permutation of the tensor's legs.  Let `a` be the leg that is
+// contiguous in the destination and `b` the leg contiguous in the source.
+// When a != b, 32 x 32 tiles over (a, b) go through shared memory so that the
+// reads run along b and the writes along a, both coalesced; when a == b the
+// copy runs along that leg directly.  The offsets of the remaining legs are
+// decoded once per tile.
 // ---------------------------------------------------------------------------
-template <int PREC>
-__global__ void __launch_bounds__(256) permute_kernel(const double* __restrict__ src, void* dst,
-                                                      int64_t plane, const __grid_constant__ PermuteStep p) {
-  for (int64_t r = blockIdx.y; r < p.rows; r += gridDim.y) {
-    const int64_t roff = legmap_offset(p.row_src, r);
-    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < p.cols;
-         c += int64_t(gridDim.x) * blockDim.x) {
-      const double v = src[roff + legmap_offset(p.col_src, c)];
-      OperandStore<PREC>::store(dst, r * p.ld + c, plane, v);
-    }
+struct PermuteArgs {
+  int n_other;
+  int64_t dim[kMaxLeg], src_stride[kMaxLeg], dst_stride[kMaxLeg];  // legs other than a, b
+  int64_t da, db;          // sizes of legs a and b
+  int64_t a_src, a_dst;    // strides of leg a (a_dst is 1 unless every leg is degenerate)
+  int64_t b_src, b_dst;    // strides of leg b (b_src is 1 likewise)
+  int64_t outer;           // product of the other legs' sizes
+};
+
+__device__ __forceinline__ void decode_other(const PermuteArgs& p, int64_t o, int64_t& so, int64_t& dof) {
+  so = 0;
+  dof = 0;
+#pragma unroll 1
+  for (int i = p.n_other - 1; i >= 0; --i) {
+    const int64_t q = o / p.dim[i];
+    const int64_t x = o - q * p.dim[i];
+    so += x * p.src_stride[i];
+    dof += x * p.dst_stride[i];
+    o = q;
   }
 }
 
-cudaError_t launch_permute(const PermuteStep& p, const double* src, void* dst, int64_t plane_elems,
+// Tiles of TA x TB (a, b) elements, TA, TB <= 32; several tiles (consecutive
+// outer indices) per block pass so that a pass moves up to 1024 elements.
+template <int PREC>
+__global__ void __launch_bounds__(256) permute_tile_kernel(const double* __restrict__ src, void* dst, int64_t plane,
+                                                           const __grid_constant__ PermuteArgs p) {
+  __shared__ double tile[2048 + 64];  // nb * TA * (TB + 1) <= 1024 (1 + 1/TB)
+  __shared__ int64_t s_src[64], s_dst[64];
+  const int TA = int(p.da < 32 ? p.da : 32), TB = int(p.db < 32 ? p.db : 32);
+  const int per_tile = TA * TB;
+  const int nb = 1024 / per_tile < 64 ? 1024 / per_tile : 64;  // tiles per pass
+  const int64_t ca = (p.da + TA - 1) / TA, cb = (p.db + TB - 1) / TB;
+  const int64_t total = p.outer * ca * cb;
+  const int tid = threadIdx.x;
+  for (int64_t t0 = int64_t(blockIdx.x) * nb; t0 < total; t0 += int64_t(gridDim.x) * nb) {
+    if (tid < nb && t0 + tid < total) {
+      const int64_t t = t0 + tid;
+      const int64_t o = t / (ca * cb);
+      const int64_t rem = t - o * ca * cb;
+      const int64_t a0 = (rem / cb) * TA, b0 = (rem % cb) * TB;
+      int64_t so, dof;
+      decode_other(p, o, so, dof);
+      s_src[tid] = so + a0 * p.a_src + b0 * p.b_src;
+      s_dst[tid] = dof + a0 * p.a_dst + b0 * p.b_dst;
+    }
+    __syncthreads();
+    const int ntiles = int(total - t0 < nb ? total - t0 : nb);
+    // read along b (contiguous in the source)
+    for (int e = tid; e < ntiles * per_tile; e += 256) {
+      const int j = e / per_tile, r = e - j * per_tile;
+      const int ia = r / TB, ib = r - ia * TB;
+      const int64_t t = t0 + j;
+      const int64_t rem = t % (ca * cb);
+      const bool ok = (rem / cb) * TA + ia < p.da && (rem % cb) * TB + ib < p.db;
+      tile[j * TA * (TB + 1) + ia * (TB + 1) + ib] = ok ? src[s_src[j] + ia * p.a_src + ib * p.b_src] : 0.0;
+    }
+    __syncthreads();
+    // write along a (contiguous in the destination)
+    for (int e = tid; e < ntiles * per_tile; e += 256) {
+      const int j = e / per_tile, r = e - j * per_tile;
+      const int ib = r / TA, ia = r - ib * TA;
+      const int64_t t = t0 + j;
+      const int64_t rem = t % (ca * cb);
+      if ((rem / cb) * TA + ia < p.da && (rem % cb) * TB + ib < p.db)
+        OperandStore<PREC>::store(dst, s_dst[j] + ib * p.b_dst + ia * p.a_dst, plane,
+                                  tile[j * TA * (TB + 1) + ia * (TB + 1) + ib]);
+    }
+    __syncthreads();
+  }
+}
+
+// a == b: lines along the common contiguous leg (size da), one warp per line chunk.
+template <int PREC>
+__global__ void __launch_bounds__(256) permute_line_kernel(const double* __restrict__ src, void* dst, int64_t plane,
+                                                           const __grid_constant__ PermuteArgs p) {
+  const int64_t chunks = (p.da + 31) / 32;
+  const int64_t total = p.outer * chunks;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32;
+  const int64_t nwarps = int64_t(gridDim.x) * blockDim.x / 32;
+  const int lane = threadIdx.x % 32;
+  for (int64_t t = warp; t < total; t += nwarps) {
+    const int64_t o = t / chunks;
+    const int64_t i = (t - o * chunks) * 32 + lane;
+    int64_t so, dof;
+    decode_other(p, o, so, dof);
+    if (i < p.da) OperandStore<PREC>::store(dst, dof + i * p.a_dst, plane, src[so + i * p.a_src]);
+  }
+}
+
+cudaError_t launch_permute(const PermuteStep& st, const double* src, void* dst, int64_t plane_elems,
                            int prec, cudaStream_t stream) {
-  if (p.rows <= 0 || p.cols <= 0) return cudaSuccess;
-  dim3 block(256);
-  dim3 grid(unsigned(std::min<int64_t>((p.cols + 255) / 256, 64)), unsigned(std::min<int64_t>(p.rows, 65535)));
+  if (st.rows <= 0 || st.cols <= 0) return cudaSuccess;
+  // Every leg with its source and destination strides.
+  int n = 0;
+  int64_t dim[2 * kMaxLeg], ss[2 * kMaxLeg], ds[2 * kMaxLeg];
+  int64_t acc = st.ld;
+  for (int i = st.row_src.n - 1; i >= 0; --i) {
+    dim[n] = st.row_src.dim[i];
+    ss[n] = st.row_src.stride[i];
+    ds[n] = acc;
+    acc *= dim[n];
+    ++n;
+  }
+  acc = 1;
+  for (int i = st.col_src.n - 1; i >= 0; --i) {
+    dim[n] = st.col_src.dim[i];
+    ss[n] = st.col_src.stride[i];
+    ds[n] = acc;
+    acc *= dim[n];
+    ++n;
+  }
+  // a: smallest destination stride, b: smallest source stride (legs of size
+  // 1 are skipped unless every leg has size 1).
+  int a = 0, b = 0;
+  for (int i = 1; i < n; ++i) {
+    const bool ai = dim[i] > 1, aa = dim[a] > 1;
+    if ((ai && !aa) || (ai == aa && ds[i] < ds[a])) a = i;
+    if ((ai && !(dim[b] > 1)) || (ai == (dim[b] > 1) && ss[i] < ss[b])) b = i;
+  }
+  PermuteArgs p{};
+  p.da = dim[a];
+  p.db = dim[b];
+  p.a_src = ss[a];
+  p.a_dst = ds[a];
+  p.b_src = ss[b];
+  p.b_dst = ds[b];
+  p.outer = 1;
+  // other legs, outermost first (order is irrelevant for correctness)
+  for (int i = n - 1; i >= 0; --i) {
+    if (i == a || i == b) continue;
+    if (p.n_other >= kMaxLeg) return cudaErrorInvalidValue;
+    p.dim[p.n_other] = dim[i];
+    p.src_stride[p.n_other] = ss[i];
+    p.dst_stride[p.n_other] = ds[i];
+    p.outer *= dim[i];
+    ++p.n_other;
+  }
   count_launch();
+  const bool line = (a == b);
+  const int64_t work = line ? p.outer * ((p.da + 31) / 32) : p.outer * ((p.da + 31) / 32) * ((p.db + 31) / 32);
+  const int64_t ta = std::min<int64_t>(p.da, 32), tb = std::min<int64_t>(p.db, 32);
+  const int64_t per_pass = std::min<int64_t>(std::max<int64_t>(1024 / (ta * tb), 1), 64);
+  const unsigned grid = unsigned(std::max<int64_t>(
+      1, std::min<int64_t>(line ? (work + 7) / 8 : (work + per_pass - 1) / per_pass, 152 * 16)));
+#define MERA_PERMUTE_LAUNCH(P)                                                                  \
+  if (line)                                                                                     \
+    permute_line_kernel<P><<<grid, 256, 0, stream>>>(src, dst, plane_elems, p);                \
+  else                                                                                          \
+    permute_tile_kernel<P><<<grid, 256, 0, stream>>>(src, dst, plane_elems, p);
   switch (prec) {
-    case PREC_F64: permute_kernel<PREC_F64><<<grid, block, 0, stream>>>(src, dst, plane_elems, p); break;
-    case PREC_TF32: permute_kernel<PREC_TF32><<<grid, block, 0, stream>>>(src, dst, plane_elems, p); break;
-    case PREC_BF16: permute_kernel<PREC_BF16><<<grid, block, 0, stream>>>(src, dst, plane_elems, p); break;
-    case PREC_BF16X3: permute_kernel<PREC_BF16X3><<<grid, block, 0, stream>>>(src, dst, plane_elems, p); break;
+    case PREC_F64: MERA_PERMUTE_LAUNCH(PREC_F64) break;
+    case PREC_TF32: MERA_PERMUTE_LAUNCH(PREC_TF32) break;
+    case PREC_BF16: MERA_PERMUTE_LAUNCH(PREC_BF16) break;
+    case PREC_BF16X3: MERA_PERMUTE_LAUNCH(PREC_BF16X3) break;
+    case PREC_BF16X6: MERA_PERMUTE_LAUNCH(PREC_BF16X6) break;
     default: return cudaErrorInvalidValue;
   }
+#undef MERA_PERMUTE_LAUNCH
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// FP64 GEMM.  64 x 64 tile per block of 256 threads, 4 x 4 outputs per
+// FP64 GEMM.  (16 T) x (16 T) tile per block of 256 threads, T x T outputs per
 // thread at stride 16 (conflict-free shared-memory reads), K in steps of 16.
+// T = 4 for large problems; T = 2 or 1 when the tile count would leave most
+// of the 152 SMs idle (the small square products of the polar iteration).
 // ---------------------------------------------------------------------------
-constexpr int kBM = 64, kBN = 64, kBK = 16;
+constexpr int kBK = 16;
 
+template <int T>
 __global__ void __launch_bounds__(256) gemm_f64_kernel(const __grid_constant__ GemmF64Args p) {
-  __shared__ double As[kBK][kBM + 1];
-  __shared__ double Bs[kBK][kBN + 1];
-  __shared__ int64_t offm[kBM];
-  __shared__ int64_t offn[kBN];
+  constexpr int R = 16 * T;
+  __shared__ double As[kBK][R + 1];
+  __shared__ double Bs[kBK][R + 1];
+  __shared__ int64_t offm[R];
+  __shared__ int64_t offn[R];
+  if (p.skip_if && *p.skip_if) return;
 
   const int tid = threadIdx.x;
-  const int64_t tiles_n = (p.N + kBN - 1) / kBN;
+  const int64_t tiles_n = (p.N + R - 1) / R;
   const int64_t tile = blockIdx.x;
-  const int64_t m0 = (tile / tiles_n) * kBM;
-  const int64_t n0 = (tile % tiles_n) * kBN;
+  const int64_t m0 = (tile / tiles_n) * R;
+  const int64_t n0 = (tile % tiles_n) * R;
   const int tx = tid % 16, ty = tid / 16;
 
-  double acc[4][4];
+  double acc[T][T];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < T; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < T; ++j) acc[i][j] = 0.0;
 
   const bool a_kfast = (p.a_k == 1);
   const bool b_kfast = (p.b_k == 1);
 
   for (int64_t k0 = 0; k0 < p.K; k0 += kBK) {
-    // A tile: 64 rows x 16 k.  Pick the thread mapping along the unit stride.
+    // R rows x 16 k per operand, T elements per thread, along the unit stride.
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < T; ++i) {
       int r, k;
       if (a_kfast) {
         k = tid % 16;
         r = tid / 16 + 16 * i;
       } else {
-        r = tid % 64;
-        k = tid / 64 + 4 * i;
+        r = tid % R;
+        k = tid / R + (256 / R) * i;
       }
       const int64_t gm = m0 + r, gk = k0 + k;
       As[k][r] = (gm < p.M && gk < p.K) ? p.A[gm * p.a_m + gk * p.a_k] : 0.0;
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < T; ++i) {
       int r, k;
       if (b_kfast) {
         k = tid % 16;
         r = tid / 16 + 16 * i;
       } else {
-        r = tid % 64;
-        k = tid / 64 + 4 * i;
+        r = tid % R;
+        k = tid / R + (256 / R) * i;
       }
       const int64_t gn = n0 + r, gk = k0 + k;
       Bs[k][r] = (gn < p.N && gk < p.K) ? p.B[gn * p.b_n + gk * p.b_k] : 0.0;
@@ -98,33 +242,35 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const __grid_constant__ G
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kBK; ++k) {
-      double a[4], b[4];
+      double a[T], b[T];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+      for (int i = 0; i < T; ++i) a[i] = As[k][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+      for (int j = 0; j < T; ++j) b[j] = Bs[k][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < T; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < T; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 
-  if (tid < kBM) {
-    const int64_t gm = m0 + tid;
-    offm[tid] = gm < p.M ? legmap_offset(p.m_dst, gm) : 0;
-  } else if (tid < kBM + kBN) {
-    const int64_t gn = n0 + tid - kBM;
-    offn[tid - kBM] = gn < p.N ? legmap_offset(p.n_dst, gn) : 0;
+  for (int t = tid; t < 2 * R; t += 256) {
+    if (t < R) {
+      const int64_t gm = m0 + t;
+      offm[t] = gm < p.M ? legmap_offset(p.m_dst, gm) : 0;
+    } else {
+      const int64_t gn = n0 + t - R;
+      offn[t - R] = gn < p.N ? legmap_offset(p.n_dst, gn) : 0;
+    }
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < T; ++i) {
     const int r = ty + 16 * i;
     if (m0 + r >= p.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < T; ++j) {
       const int c = tx + 16 * j;
       if (n0 + c >= p.N) continue;
       double* dst = p.C + offm[r] + offn[c];
@@ -136,10 +282,17 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const __grid_constant__ G
 
 cudaError_t launch_gemm_f64(const GemmF64Args& args, cudaStream_t stream) {
   if (args.M <= 0 || args.N <= 0) return cudaSuccess;
-  const int64_t tiles = ((args.M + kBM - 1) / kBM) * ((args.N + kBN - 1) / kBN);
-  if (tiles > 0x7fffffff) return cudaErrorInvalidValue;
+  auto tiles = [&](int64_t r) { return ((args.M + r - 1) / r) * ((args.N + r - 1) / r); };
+  constexpr int64_t kFill = 2 * 152;  // enough blocks to occupy every SM twice
   count_launch();
-  gemm_f64_kernel<<<unsigned(tiles), 256, 0, stream>>>(args);
+  if (tiles(64) >= kFill || tiles(32) > 0x7fffffff) {
+    if (tiles(64) > 0x7fffffff) return cudaErrorInvalidValue;
+    gemm_f64_kernel<4><<<unsigned(tiles(64)), 256, 0, stream>>>(args);
+  } else if (tiles(32) >= kFill) {
+    gemm_f64_kernel<2><<<unsigned(tiles(32)), 256, 0, stream>>>(args);
+  } else {
+    gemm_f64_kernel<1><<<unsigned(tiles(16)), 256, 0, stream>>>(args);
+  }
   return cudaGetLastError();
 }
 
@@ -308,7 +461,8 @@ cudaError_t launch_frob_scale(const double* src, double* dst, int64_t count, dou
 
 // Bm = (3 I - G) / 2 and partial sums of ||G - I||_F^2.
 __global__ void __launch_bounds__(256) ns_combine_kernel(const double* __restrict__ G, double* Bm, int64_t n,
-                                                         double* partials) {
+                                                         double* partials, const int* skip_if) {
+  if (skip_if && *skip_if) return;
   double v = 0.0;
   const int64_t count = n * n;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x) {
@@ -322,12 +476,39 @@ __global__ void __launch_bounds__(256) ns_combine_kernel(const double* __restric
   if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }
 
-cudaError_t launch_ns_combine(const double* G, double* Bm, int64_t n, double* partials, double* resid,
-                              cudaStream_t stream) {
+// state[0] = done, state[1] = iterations executed, state[2] = converged after
+// this iteration; resid = ||X^T X - I||_F of the iterate entering it.
+__global__ void __launch_bounds__(1024) ns_check_kernel(const double* __restrict__ partials, int np, double* resid,
+                                                        double tol, int* state) {
+  if (state[0]) return;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) v += partials[i];
+  v = block_sum<1024>(v);
+  if (threadIdx.x == 0) {
+    const double r = sqrt(v);
+    *resid = r;
+    state[2] = (r <= tol || !(r == r)) ? 1 : 0;  // converged, or NaN: stop after this step
+  }
+}
+
+__global__ void ns_finish_kernel(int* state) {
+  if (state[0]) return;
+  state[1] += 1;
+  if (state[2]) state[0] = 1;
+}
+
+cudaError_t launch_ns_step(const double* G, double* Bm, int64_t n, double* partials, double* resid, double tol,
+                           int* state, cudaStream_t stream) {
   const int nb = int(std::min<int64_t>((n * n + 255) / 256, 1024));
   count_launch(2);
-  ns_combine_kernel<<<nb, 256, 0, stream>>>(G, Bm, n, partials);
-  reduce_partials_kernel<<<1, 1024, 0, stream>>>(partials, nb, resid, 1);
+  ns_combine_kernel<<<nb, 256, 0, stream>>>(G, Bm, n, partials, state);
+  ns_check_kernel<<<1, 1024, 0, stream>>>(partials, nb, resid, tol, state);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ns_finish(int* state, cudaStream_t stream) {
+  count_launch();
+  ns_finish_kernel<<<1, 1, 0, stream>>>(state);
   return cudaGetLastError();
 }
 

@@ -21,7 +21,29 @@ int elem_bytes(int prec) {
     default: return 2;
   }
 }
-int planes(int prec) { return prec == PREC_BF16X3 ? 2 : 1; }
+int tc_block_n(int prec, int64_t N) {
+  if (N > 128) return prec == PREC_BF16X6 ? 128 : 256;
+  if (N > 64) return 128;
+  if (N > 32) return 64;
+  if (N > 16) return 32;
+  return 16;
+}
+
+int tc_split_k(int prec, int64_t M, int64_t N, int64_t K) {
+  if (prec == PREC_F64) return 1;
+  constexpr int64_t kSMs = 152;
+  const int64_t bn = tc_block_n(prec, N);
+  const int64_t tiles = ((M + 127) / 128) * ((N + bn - 1) / bn);
+  const int64_t bk = 128 / elem_bytes(prec);
+  const int64_t num_k = (K + bk - 1) / bk;
+  if (tiles >= kSMs || num_k < 8) return 1;
+  int64_t s = std::min<int64_t>((2 * kSMs + tiles - 1) / tiles, num_k / 4);
+  s = std::max<int64_t>(s, 1);
+  const int64_t kc = (num_k + s - 1) / s;
+  return int((num_k + kc - 1) / kc);  // every split non-empty
+}
+
+int planes(int prec) { return prec == PREC_BF16X3 ? 2 : (prec == PREC_BF16X6 ? 3 : 1); }
 
 namespace {
 
@@ -407,6 +429,18 @@ struct Builder {
       gs.alpha = (i == tr.root) ? alpha : 1.0;
       gs.accumulate = (i == tr.root) ? accumulate : 0;
       gs.flops = 2.0 * double(gs.M) * double(gs.N) * double(gs.K);
+      gs.split = tc_split_k(prec, gs.M, gs.N, gs.K);
+      if (gs.split > 1) {  // FP32 partials [split][N][M], live during this step only
+        Buffer pb;
+        pb.rows = int64_t(gs.split) * gs.N;
+        pb.ld = gs.M;
+        pb.plane_bytes = round_up(pb.rows * pb.ld * 4, 256);
+        pb.bytes = pb.plane_bytes;
+        prog.bufs.push_back(pb);
+        gs.p_buf = int(prog.bufs.size()) - 1;
+        first_use.push_back(-1);
+        last_use.push_back(-1);
+      }
       {
         std::vector<int> kl = gi.klegs;
         auto a_legs = gi.mlegs;
@@ -426,6 +460,7 @@ struct Builder {
       const int si = int(prog.steps.size()) - 1;
       last_use[gs.a_buf] = si;
       last_use[gs.b_buf] = si;
+      if (gs.p_buf >= 0) first_use[gs.p_buf] = last_use[gs.p_buf] = si;
       if (gs.c_buf >= 0) first_use[gs.c_buf] = si;
     }
     double fmax = 0.0;
@@ -472,7 +507,7 @@ std::map<Key, std::unique_ptr<OpProgram>> g_cache;
 
 const OpProgram* get_program(int op, int chi_b, int chi_t, int prec) {
   if (op < OP_ASCEND || op > OP_ENV_W) return nullptr;
-  if (prec < PREC_F64 || prec > PREC_BF16X3) return nullptr;
+  if (prec < PREC_F64 || prec > PREC_BF16X6) return nullptr;
   if (chi_b < 1 || chi_t < 1 || chi_b > 64 || chi_t > 64) return nullptr;
   if (chi_t > chi_b * chi_b) return nullptr;
   std::lock_guard<std::mutex> lk(g_mu);
@@ -531,7 +566,8 @@ std::string program_json(const OpProgram& prog, int op, int chi_b, int chi_t, in
         o << "{\"kind\":\"gemm\",\"label\":\"" << g.label << "\",\"a_buf\":" << g.a_buf << ",\"b_buf\":" << g.b_buf
           << ",\"M\":" << g.M << ",\"N\":" << g.N << ",\"K\":" << g.K << ",\"lda\":" << g.lda << ",\"ldb\":" << g.ldb
           << ",\"c_buf\":" << g.c_buf << ",\"alpha\":" << g.alpha << ",\"accumulate\":" << g.accumulate
-          << ",\"flops\":" << g.flops << ",\"dominant\":" << g.dominant << ",\"m_dst\":";
+          << ",\"flops\":" << g.flops << ",\"dominant\":" << g.dominant << ",\"split\":" << g.split
+          << ",\"p_buf\":" << g.p_buf << ",\"m_dst\":";
         lm(g.m_dst);
         o << ",\"n_dst\":";
         lm(g.n_dst);

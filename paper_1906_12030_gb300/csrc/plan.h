@@ -17,7 +17,7 @@
 
 namespace mera {
 
-enum Prec : int { PREC_F64 = 0, PREC_TF32 = 1, PREC_BF16 = 2, PREC_BF16X3 = 3 };
+enum Prec : int { PREC_F64 = 0, PREC_TF32 = 1, PREC_BF16 = 2, PREC_BF16X3 = 3, PREC_BF16X6 = 4 };
 enum Slot : int { SLOT_OP = 0, SLOT_RHO = 1, SLOT_U = 2, SLOT_W = 3 };
 enum Op : int { OP_ASCEND = 0, OP_DESCEND = 1, OP_ENV_U = 2, OP_ENV_W = 3 };
 
@@ -52,6 +52,8 @@ struct GemmStep {
   int accumulate = 0;
   double flops = 0.0;
   int dominant = 0;   // one of the chi^9-class steps of its diagram
+  int split = 1;      // K split over this many CTAs (tensor-core modes; partials summed in FP64)
+  int p_buf = -1;     // FP32 partial-sum buffer [split][N][M] when split > 1
   std::string label;  // e.g. "aceiq*CDcdil->ADadelq" for inspection
 };
 
@@ -86,7 +88,12 @@ struct OpProgram {
 };
 
 int elem_bytes(int prec);   // storage bytes of one operand element (one plane)
-int planes(int prec);       // 2 for BF16X3 (hi, lo), else 1
+// Output-tile width of the tensor-core GEMM for an N-column product.
+int tc_block_n(int prec, int64_t N);
+// K split of a tensor-core GEMM: > 1 when too few output tiles would leave
+// most SMs idle and K is long (each split keeps >= 4 k-blocks).
+int tc_split_k(int prec, int64_t M, int64_t N, int64_t K);
+int planes(int prec);       // 2 for BF16X3 (hi, lo), 3 for BF16X6 (hi, mid, lo), else 1
 
 // Builds (and caches) the program; thread safe.  Returns nullptr on bad input.
 const OpProgram* get_program(int op, int chi_b, int chi_t, int prec);

@@ -2,12 +2,17 @@
 // K-major) -> tcgen05.mma (FP32 accumulator in tensor memory) -> scattered
 // epilogue that writes the next contraction's operand layout directly.
 //
-// One CTA computes one 128 x BN output tile.  Warp roles:
-//   warp 0      TMA producer (one elected lane), STAGES-deep ring
+// Persistent kernel: each CTA walks output tiles (128 x BN) t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...  Tensor memory holds two accumulators, so the
+// epilogue of one tile overlaps the MMAs of the next.  Warp roles:
+//   warp 0      TMA producer (one elected lane), STAGES-deep ring shared by
+//               all of the CTA's tiles
 //   warp 1      tensor-memory allocator + MMA issuer (one lane)
-//   warps 2..5  epilogue: tcgen05.ld of the accumulator, convert, store
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator, convert, store; the
+//               accumulator is handed back to the MMA warp after its last load
 // Every mbarrier wait is bounded; a wait that gives up records
-// MERA_ETIMEOUT in a device status word and the CTA drains and exits.
+// MERA_ETIMEOUT in a device status word, raises a CTA-wide abort flag, and
+// every role drains its copies in flight and leaves.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -64,16 +69,26 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Bounded wait on the phase with the given parity; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait on the phase with the given parity.  Gives up (false) when
+// the CTA's abort flag is raised or after kTimeoutNs; a timeout raises the
+// flag and records MERA_ETIMEOUT.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t i = 1; i < kSpinCap; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255u) == 0 && global_ns() - t0 > kTimeoutNs) break;
+    if ((i & 255u) == 0) {
+      if (*abort_flag) return false;
+      if (global_ns() - t0 > kTimeoutNs) break;
+    }
   }
   atomicOr(&g_device_status, 1 << MERA_ETIMEOUT);
+  *abort_flag = 1;
   return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
@@ -138,6 +153,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Operand tensor maps, one per plane (hi, lo / hi, mid, lo for split modes).
+struct TMaps {
+  CUtensorMap a[3];
+  CUtensorMap b[3];
+};
+
 struct Epilogue {
   int64_t M, N, K;
   void* C;
@@ -146,27 +167,29 @@ struct Epilogue {
   double alpha;
   int accumulate;
   int c_final;      // 1: FP64 output of the caller
+  int split;        // K split: work item t covers output tile t % tiles and k-range t / tiles
+  int kc;           // k-blocks per split
+  float* partial;   // split > 1: raw FP32 partials [split][N][M], summed by splitk_reduce_kernel
 };
 
 template <int PREC, int BN>
 struct Cfg {
   static constexpr int kElem = (PREC == PREC_TF32) ? 4 : 2;
   static constexpr int kBK = kSlabBytes / kElem;          // K per stage
-  static constexpr int kPlanes = (PREC == PREC_BF16X3) ? 2 : 1;
+  static constexpr int kPlanes = (PREC == PREC_BF16X3) ? 2 : (PREC == PREC_BF16X6 ? 3 : 1);
   static constexpr int kABytes = kBM * kSlabBytes;        // one plane of A
   static constexpr int kBBytes = BN * kSlabBytes;
   static constexpr int kStageBytes = kPlanes * (kABytes + kBBytes);
-  static constexpr int kStages = (PREC == PREC_BF16X3) ? (BN >= 256 ? 2 : 3) : 4;
-  static constexpr int kTmemCols = BN < 32 ? 32 : BN;
+  static constexpr int kStages = (kPlanes == 1) ? 4 : (kPlanes == 2 ? (BN >= 256 ? 2 : 3) : (BN >= 128 ? 2 : 3));
+  static constexpr int kAccCols = BN < 32 ? 32 : BN;     // one accumulator
+  static constexpr int kTmemCols = 2 * kAccCols;            // two, double-buffered
   static constexpr uint32_t kFmt = (PREC == PREC_TF32) ? 2u : 1u;  // TF32 / BF16
   static constexpr size_t kSmem = 1024 + size_t(kStages) * kStageBytes + 1024 + BN * sizeof(int64_t);
 };
 
 template <int PREC, int BN>
 __global__ void __launch_bounds__(kThreads, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
-                   const __grid_constant__ Epilogue ep) {
+    tc_gemm_kernel(const __grid_constant__ TMaps tm, const __grid_constant__ Epilogue ep) {
   using C = Cfg<PREC, BN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -174,15 +197,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* aux = smem + size_t(C::kStages) * C::kStageBytes;
   uint64_t* full = reinterpret_cast<uint64_t*>(aux);
   uint64_t* empty = full + C::kStages;
-  uint64_t* accum = empty + C::kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
-  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  uint64_t* acc_full = empty + C::kStages;   // [2] MMA -> epilogue
+  uint64_t* acc_empty = acc_full + 2;        // [2] epilogue -> MMA
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* abort_snapshot = abort_flag + 1;
+  volatile int* never = abort_flag + 2;  // stays 0: waits that must not be cut short
   int64_t* off_n = reinterpret_cast<int64_t*>(aux + 1024);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t tiles_n = (ep.N + BN - 1) / BN;
-  const int64_t m0 = (int64_t(blockIdx.x) / tiles_n) * kBM;
-  const int64_t n0 = (int64_t(blockIdx.x) % tiles_n) * BN;
+  const int64_t tiles_mn = ((ep.M + kBM - 1) / kBM) * tiles_n;
+  const int64_t tiles = tiles_mn * ep.split;
   const int num_k = int((ep.K + C::kBK - 1) / C::kBK);
 
   if (threadIdx.x == 0) {
@@ -190,8 +216,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);  // one arrive per epilogue warp
+    }
     *abort_flag = 0;
+    *abort_snapshot = 0;
+    *never = 0;
     fence_barrier_init();
   }
   if (warp == 1) {
@@ -208,81 +239,121 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---- producer ---------------------------------------------------------
-      int issued = 0;
-      for (int kb = 0; kb < num_k; ++kb) {
-        const int s = kb % C::kStages;
-        if (kb >= C::kStages) {
-          if (!mbar_wait(&empty[s], ((kb / C::kStages) & 1) ^ 1)) {
-            *reinterpret_cast<volatile int*>(abort_flag) = 1;
+      uint32_t it = 0;
+      bool alive = true;
+      for (int64_t t = blockIdx.x; t < tiles && alive; t += gridDim.x) {
+        const int64_t mn = t % tiles_mn;
+        const int m0 = int((mn / tiles_n) * kBM), n0 = int((mn % tiles_n) * BN);
+        const int kb0 = int(t / tiles_mn) * ep.kc, kb1 = min(kb0 + ep.kc, num_k);
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+          const uint32_t s = it % C::kStages;
+          if (it >= uint32_t(C::kStages) && !mbar_wait(&empty[s], ((it / C::kStages) & 1) ^ 1, abort_flag)) {
+            alive = false;
             break;
           }
+          uint8_t* st = stage_base + size_t(s) * C::kStageBytes;
+          mbar_arrive_expect_tx(&full[s], C::kStageBytes);
+          const int x = kb * C::kBK;
+#pragma unroll
+          for (int pl = 0; pl < C::kPlanes; ++pl) {  // plane pl: A then B
+            uint8_t* dst = st + pl * (C::kABytes + C::kBBytes);
+            tma_load_2d(dst, &tm.a[pl], x, m0, &full[s]);
+            tma_load_2d(dst + C::kABytes, &tm.b[pl], x, n0, &full[s]);
+          }
         }
-        if (*reinterpret_cast<volatile int*>(abort_flag)) break;
-        uint8_t* st = stage_base + size_t(s) * C::kStageBytes;
-        mbar_arrive_expect_tx(&full[s], C::kStageBytes);
-        const int x = kb * C::kBK;
-        tma_load_2d(st, &tmA, x, int(m0), &full[s]);
-        tma_load_2d(st + C::kABytes, &tmB, x, int(n0), &full[s]);
-        if constexpr (C::kPlanes == 2) {
-          tma_load_2d(st + C::kABytes + C::kBBytes, &tmA2, x, int(m0), &full[s]);
-          tma_load_2d(st + 2 * C::kABytes + C::kBBytes, &tmB2, x, int(n0), &full[s]);
-        }
-        ++issued;
       }
       // drain: every issued stage must have landed before the CTA may exit
-      for (int kb = (issued > C::kStages ? issued - C::kStages : 0); kb < issued; ++kb)
-        mbar_wait(&full[kb % C::kStages], (kb / C::kStages) & 1);
+      for (uint32_t j = (it > uint32_t(C::kStages) ? it - C::kStages : 0); j < it; ++j)
+        mbar_wait(&full[j % C::kStages], (j / C::kStages) & 1, never);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer -------------------------------------------------------
       constexpr uint32_t idesc = make_idesc(C::kFmt, kBM, BN < 16 ? 16 : BN);
-      for (int kb = 0; kb < num_k; ++kb) {
-        const int s = kb % C::kStages;
-        if (!mbar_wait(&full[s], (kb / C::kStages) & 1)) {
-          *reinterpret_cast<volatile int*>(abort_flag) = 1;
-          break;
-        }
+      uint32_t it = 0, tc = 0;
+      bool alive = true;
+      for (int64_t t = blockIdx.x; t < tiles && alive; t += gridDim.x, ++tc) {
+        const uint32_t b = tc & 1;
+        if (tc >= 2 && !mbar_wait(&acc_empty[b], ((tc >> 1) - 1) & 1, abort_flag)) break;
         tc_fence_after();
-        const uint32_t sa = smem_u32(stage_base + size_t(s) * C::kStageBytes);
-        const uint32_t sb = sa + C::kABytes;
-#pragma unroll
-        for (int k = 0; k < kSlabBytes / 32; ++k) {
-          const uint32_t koff = uint32_t(k * 32);
-          const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-          tc_mma<PREC>(tmem, sw128_desc(sa + koff), sw128_desc(sb + koff), idesc, acc);
-          if constexpr (C::kPlanes == 2) {
-            const uint32_t sa2 = sb + C::kBBytes, sb2 = sa2 + C::kABytes;
-            tc_mma<PREC>(tmem, sw128_desc(sa + koff), sw128_desc(sb2 + koff), idesc, 1u);   // hi * lo
-            tc_mma<PREC>(tmem, sw128_desc(sa2 + koff), sw128_desc(sb + koff), idesc, 1u);   // lo * hi
+        const uint32_t d = tmem + b * uint32_t(C::kAccCols);
+        const int kb0 = int(t / tiles_mn) * ep.kc, kb1 = min(kb0 + ep.kc, num_k);
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+          const uint32_t s = it % C::kStages;
+          if (!mbar_wait(&full[s], (it / C::kStages) & 1, abort_flag)) {
+            alive = false;
+            break;
           }
+          tc_fence_after();
+          const uint32_t s0 = smem_u32(stage_base + size_t(s) * C::kStageBytes);
+          constexpr uint32_t kPlaneStride = C::kABytes + C::kBBytes;
+#pragma unroll
+          for (int k = 0; k < kSlabBytes / 32; ++k) {
+            const uint32_t koff = uint32_t(k * 32);
+            // products of A plane pa and B plane pb with pa + pb < planes:
+            // (0,0) | (0,0) (0,1) (1,0) | (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+#pragma unroll
+            for (int pa = 0; pa < C::kPlanes; ++pa) {
+#pragma unroll
+              for (int pb = 0; pb + pa < C::kPlanes; ++pb) {
+                const uint32_t a_addr = s0 + pa * kPlaneStride + koff;
+                const uint32_t b_addr = s0 + pb * kPlaneStride + C::kABytes + koff;
+                const uint32_t acc = (kb > kb0 || k > 0 || pa > 0 || pb > 0) ? 1u : 0u;
+                tc_mma<PREC>(d, sw128_desc(a_addr), sw128_desc(b_addr), idesc, acc);
+              }
+            }
+          }
+          tc_commit(&empty[s]);
         }
-        tc_commit(&empty[s]);
+        tc_commit(&acc_full[b]);  // also fires after an abort, so nobody waits on it forever
       }
-      tc_commit(accum);
     }
   } else {
     // ---- epilogue (warps 2..5) -------------------------------------------------
     const int et = threadIdx.x - 64;  // 0..127
-    for (int c = et; c < BN; c += 128) {
-      const int64_t n = n0 + c;
-      off_n[c] = n < ep.N ? legmap_offset(ep.n_dst, n) : 0;
-    }
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    const int quarter = warp % 4;  // tensor-memory lanes this warp may read
+    const int quarter = warp % 4;     // tensor-memory lanes this warp may read
     const int row = quarter * 32 + lane;
-    const int64_t m = m0 + row;
-    const bool row_ok = m < ep.M;
-    const int64_t off_m = row_ok ? legmap_offset(ep.m_dst, m) : 0;
-    const bool ok = mbar_wait(accum, 0);
-    tc_fence_after();
-    if (ok && !*reinterpret_cast<volatile int*>(abort_flag)) {
-      const float alpha = float(ep.alpha);
+    const float alpha = float(ep.alpha);
+    uint32_t tc = 0;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++tc) {
+      const int64_t mn = t % tiles_mn, ks = t / tiles_mn;
+      const int64_t m0 = (mn / tiles_n) * kBM, n0 = (mn % tiles_n) * BN;
+      const uint32_t b = tc & 1;
+      // all epilogue threads are done with the previous tile's off_n; decide
+      // together whether to go on
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (et == 0) *abort_snapshot = *abort_flag;
+      for (int c = et; c < BN; c += 128) {
+        const int64_t n = n0 + c;
+        off_n[c] = n < ep.N ? legmap_offset(ep.n_dst, n) : 0;
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (*abort_snapshot) break;
+      const int64_t m = m0 + row;
+      const bool row_ok = m < ep.M;
+      const int64_t off_m = row_ok ? legmap_offset(ep.m_dst, m) : 0;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], (tc >> 1) & 1, abort_flag) ? 1 : 0);
+      tc_fence_after();
+      if (!ok) continue;  // the next snapshot sees the abort flag
+      const uint32_t taddr = tmem + b * uint32_t(C::kAccCols) + (uint32_t(quarter * 32) << 16);
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t v[32];
-        tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(c0), v);
+        tmem_ld32(taddr + uint32_t(c0), v);
+        if (c0 + 32 >= BN) {  // last read of this accumulator: hand it back
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
         if (!row_ok) continue;
+        if (ep.split > 1) {  // raw partial sums, reduced in FP64 afterwards
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t n = n0 + c0 + j;
+            if (c0 + j < BN && n < ep.N) ep.partial[(ks * ep.N + n) * ep.M + m] = __uint_as_float(v[j]);
+          }
+          continue;
+        }
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int c = c0 + j;
@@ -298,11 +369,20 @@ __global__ void __launch_bounds__(kThreads, 1)
               static_cast<float*>(ep.C)[off] = round_tf32(val);
             } else if constexpr (PREC == PREC_BF16) {
               static_cast<__nv_bfloat16*>(ep.C)[off] = __float2bfloat16_rn(val);
-            } else {
+            } else if constexpr (PREC == PREC_BF16X3) {
               const __nv_bfloat16 hi = __float2bfloat16_rn(val);
               const __nv_bfloat16 lo = __float2bfloat16_rn(val - __bfloat162float(hi));
               static_cast<__nv_bfloat16*>(ep.C)[off] = hi;
               static_cast<__nv_bfloat16*>(ep.C)[off + ep.c_plane] = lo;
+            } else {
+              const __nv_bfloat16 hi = __float2bfloat16_rn(val);
+              const float r1 = val - __bfloat162float(hi);
+              const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+              const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+              __nv_bfloat16* c = static_cast<__nv_bfloat16*>(ep.C);
+              c[off] = hi;
+              c[off + ep.c_plane] = mid;
+              c[off + 2 * ep.c_plane] = lo;
             }
           }
         }
@@ -315,6 +395,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(C::kTmemCols))
                  : "memory");
+  }
+}
+
+// Sum of the K-split partials in binary64 (fixed order), then the same
+// epilogue as the GEMM: alpha, conversion and scattered store.  One thread per
+// row m, looping over a chunk of columns.
+template <int PREC>
+__global__ void __launch_bounds__(256) splitk_reduce_kernel(const __grid_constant__ Epilogue ep) {
+  const int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (m >= ep.M) return;
+  const int64_t off_m = legmap_offset(ep.m_dst, m);
+  const int64_t n_per = (ep.N + gridDim.y - 1) / gridDim.y;
+  const int64_t n_lo = int64_t(blockIdx.y) * n_per, n_hi = min(ep.N, n_lo + n_per);
+  for (int64_t n = n_lo; n < n_hi; ++n) {
+    double acc = 0.0;
+    for (int s = 0; s < ep.split; ++s) acc += double(ep.partial[(int64_t(s) * ep.N + n) * ep.M + m]);
+    const double val = ep.alpha * acc;
+    const int64_t off = off_m + legmap_offset(ep.n_dst, n);
+    if (ep.c_final) {
+      double* dst = static_cast<double*>(ep.C) + off;
+      *dst = ep.accumulate ? (*dst + val) : val;
+    } else {
+      OperandStore<PREC>::store(ep.C, off, ep.c_plane, val);
+    }
   }
 }
 
@@ -359,17 +463,13 @@ cudaError_t launch_cfg(const TcGemmArgs& a, cudaStream_t stream) {
                                     int(C::kSmem));
   });
   if (attr_err != cudaSuccess) return attr_err;
-  CUtensorMap tA, tB, tA2, tB2;
+  TMaps tm;
   const char* A = static_cast<const char*>(a.A);
   const char* B = static_cast<const char*>(a.B);
-  if (!encode_operand(&tA, A, PREC, a.M, a.K, a.lda, kBM)) return cudaErrorInvalidValue;
-  if (!encode_operand(&tB, B, PREC, a.N, a.K, a.ldb, BN)) return cudaErrorInvalidValue;
-  if (C::kPlanes == 2) {
-    if (!encode_operand(&tA2, A + a.a_plane_bytes, PREC, a.M, a.K, a.lda, kBM)) return cudaErrorInvalidValue;
-    if (!encode_operand(&tB2, B + a.b_plane_bytes, PREC, a.N, a.K, a.ldb, BN)) return cudaErrorInvalidValue;
-  } else {
-    tA2 = tA;
-    tB2 = tB;
+  for (int pl = 0; pl < 3; ++pl) {
+    const int q = pl < C::kPlanes ? pl : 0;  // unused slots repeat plane 0
+    if (!encode_operand(&tm.a[pl], A + q * a.a_plane_bytes, PREC, a.M, a.K, a.lda, kBM)) return cudaErrorInvalidValue;
+    if (!encode_operand(&tm.b[pl], B + q * a.b_plane_bytes, PREC, a.N, a.K, a.ldb, BN)) return cudaErrorInvalidValue;
   }
   Epilogue ep;
   ep.M = a.M;
@@ -382,16 +482,39 @@ cudaError_t launch_cfg(const TcGemmArgs& a, cudaStream_t stream) {
   ep.alpha = a.alpha;
   ep.accumulate = a.accumulate;
   ep.c_final = a.c_final ? 1 : 0;
-  const int64_t tiles = ((a.M + kBM - 1) / kBM) * ((a.N + BN - 1) / BN);
-  if (tiles <= 0 || tiles > 0x7fffffff) return cudaErrorInvalidValue;
+  const int64_t num_k = (a.K + C::kBK - 1) / C::kBK;
+  const int split = a.split > 1 && a.partial ? a.split : 1;
+  ep.split = split;
+  ep.kc = int((num_k + split - 1) / split);
+  ep.partial = a.partial;
+  if (split > 1 && (int64_t(split - 1) * ep.kc >= num_k)) return cudaErrorInvalidValue;  // empty split
+  const int64_t tiles = ((a.M + kBM - 1) / kBM) * ((a.N + BN - 1) / BN) * split;
+  if (tiles <= 0) return cudaErrorInvalidValue;
+  static int resident = 0;  // CTAs of this configuration the whole GPU holds at once
+  static std::once_flag occ_once;
+  std::call_once(occ_once, [] {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_gemm_kernel<PREC, BN>, kThreads, C::kSmem);
+    resident = std::max(1, sms) * std::max(1, per_sm);
+  });
+  const unsigned grid = unsigned(std::min<int64_t>(tiles, resident));
   count_launch();
-  tc_gemm_kernel<PREC, BN><<<unsigned(tiles), kThreads, C::kSmem, stream>>>(tA, tB, tA2, tB2, ep);
+  tc_gemm_kernel<PREC, BN><<<grid, kThreads, C::kSmem, stream>>>(tm, ep);
+  if (split > 1) {
+    const unsigned gx = unsigned((a.M + 255) / 256);
+    const unsigned gy = unsigned(std::min<int64_t>(a.N, std::max<int64_t>(1, 4 * 152 / int64_t(gx))));
+    count_launch();
+    splitk_reduce_kernel<PREC><<<dim3(gx, gy), 256, 0, stream>>>(ep);
+  }
   return cudaGetLastError();
 }
 
 template <int PREC>
 cudaError_t launch_prec(const TcGemmArgs& a, cudaStream_t stream) {
-  if (a.N > 128) return launch_cfg<PREC, 256>(a, stream);
+  // three-plane operands: a 256-wide B tile leaves room for one stage only
+  if (a.N > 128 && PREC != PREC_BF16X6) return launch_cfg<PREC, (PREC == PREC_BF16X6 ? 128 : 256)>(a, stream);
   if (a.N > 64) return launch_cfg<PREC, 128>(a, stream);
   if (a.N > 32) return launch_cfg<PREC, 64>(a, stream);
   if (a.N > 16) return launch_cfg<PREC, 32>(a, stream);
@@ -407,6 +530,7 @@ cudaError_t launch_gemm_tc(const TcGemmArgs& a, cudaStream_t stream) {
     case PREC_TF32: return launch_prec<PREC_TF32>(a, stream);
     case PREC_BF16: return launch_prec<PREC_BF16>(a, stream);
     case PREC_BF16X3: return launch_prec<PREC_BF16X3>(a, stream);
+    case PREC_BF16X6: return launch_prec<PREC_BF16X6>(a, stream);
     default: return cudaErrorNotSupported;
   }
 }

@@ -28,6 +28,8 @@ struct TcGemmArgs {
   LegMap m_dst, n_dst;
   double alpha = 1.0;
   int accumulate = 0;
+  int split = 1;             // K split (from tc_split_k); > 1 needs `partial`
+  float* partial = nullptr;  // FP32 scratch [split][N][M]
 };
 
 cudaError_t launch_gemm_tc(const TcGemmArgs& args, cudaStream_t stream);

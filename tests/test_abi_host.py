@@ -105,10 +105,14 @@ def _emulate(plan, inputs, out_size):
     arena = np.full(plan["ws_bytes"] // eb + 1, np.nan)
     for dg in plan["diagrams"]:
         bufs = dg["bufs"]
-        for b in bufs:
+        partial = {st["p_buf"] for st in dg["steps"] if st["kind"] == "gemm" and st["p_buf"] >= 0}
+        for i, b in enumerate(bufs):
             assert b["offset"] % 256 == 0
-            assert b["ld"] * eb % 16 == 0  # TMA: row pitch multiple of 16 bytes
             assert b["offset"] + b["bytes"] <= plan["ws_bytes"]
+            if i in partial:  # FP32 split-K partials [split][N][M]
+                assert b["bytes"] >= b["rows"] * b["ld"] * 4
+            else:
+                assert b["ld"] * eb % 16 == 0  # TMA: row pitch multiple of 16 bytes
         arena[:] = np.nan  # stale data from an earlier diagram must never be read
         for st in dg["steps"]:
             if st["kind"] == "permute":
@@ -148,8 +152,12 @@ def _emulate(plan, inputs, out_size):
     return out
 
 
-@pytest.mark.parametrize("prec", [m.PREC_F64, m.PREC_BF16X3])
-@pytest.mark.parametrize("chi_b,chi_t", [(2, 2), (3, 3), (2, 3), (4, 3), (3, 5)])
+_SMALL = [(2, 2), (3, 3), (2, 3), (4, 3), (3, 5)]
+
+
+@pytest.mark.parametrize("prec,chi_b,chi_t",
+                         [(p, b, t) for p in (m.PREC_F64, m.PREC_BF16X3, m.PREC_BF16X6) for b, t in _SMALL]
+                         + [(m.PREC_BF16X3, 4, 16)])  # first-layer shape, with K-split steps
 def test_programs_reproduce_oracle(prec, chi_b, chi_t):
     rng = np.random.default_rng(20)
     u, w = I.random_u(rng, chi_b), I.random_w(rng, chi_b, chi_t)
@@ -166,3 +174,21 @@ def test_programs_reproduce_oracle(prec, chi_b, chi_t):
         plan = m.mera_plan_json(op, chi_b, chi_t, prec)
         got = _emulate(plan, inputs, want.size).reshape(want.shape)
         assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max()), op
+
+
+def test_split_k_partials_do_not_overlap_live_buffers():
+    """Steps with few output tiles and long K get a K split; its FP32 partial
+    buffer must not overlap the step's operands (the arena check above runs
+    the same programs)."""
+    plan = m.mera_plan_json(m.OP_ENV_W, 4, 16, m.PREC_BF16X3)
+    splits = [st for dg in plan["diagrams"] for st in dg["steps"] if st["kind"] == "gemm" and st["split"] > 1]
+    assert splits, "the K = 65536 step of the 4 -> 16 env_w program should be split"
+    for dg in plan["diagrams"]:
+        bufs = dg["bufs"]
+        for st in dg["steps"]:
+            if st["kind"] != "gemm" or st["split"] <= 1:
+                continue
+            p = bufs[st["p_buf"]]
+            for other in (st["a_buf"], st["b_buf"]) + ((st["c_buf"],) if st["c_buf"] >= 0 else ()):
+                o = bufs[other]
+                assert p["offset"] + p["bytes"] <= o["offset"] or o["offset"] + o["bytes"] <= p["offset"]

@@ -168,3 +168,22 @@ def test_ascend_chi16_sampled_rows_and_identity():
     m.mera_ascend(eye, ud, wd, chi, chi, out)
     a1 = out.reshape(chi ** 3, chi ** 3)
     assert (a1 - torch.eye(chi ** 3, dtype=torch.float64, device="cuda")).abs().max().item() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Scaling dimensions (Sec. II B, Fig. 7): Arnoldi with the GPU ascend as
+# matvec against the oracle's eigen-solve of the same map.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("chi", [2, 3, 4])
+def test_scaling_dimensions_match_oracle(chi):
+    from paper_1906_12030_gb300 import scaling
+
+    rng = np.random.default_rng(40 + chi)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    # Ask both for 10 eigenvalues and compare the leading 4: near the cut-off
+    # of a random map |lambda| is nearly degenerate and either solver may
+    # keep a different member of a close pair.
+    got = scaling.scaling_dimensions(_cuda(u), _cuda(w), chi, k=10)[:4]
+    want = O.scaling_dimensions(u, w, 10)[:4]
+    assert got[0] == pytest.approx(0.0, abs=1e-9)  # A(1) = 1
+    np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-8)

@@ -40,19 +40,40 @@ __device__ __forceinline__ void decode_other(const PermuteArgs& p, int64_t o, in
 
 // Tiles of TA x TB (a, b) elements, TA, TB <= 32; several tiles (consecutive
 // outer indices) per block pass so that a pass moves up to 1024 elements.
+// Each thread's in-tile coordinates are fixed for the whole kernel and each
+// tile's base offsets and extents are decoded once into shared memory, so
+// the element loops do no division.  read_a_fast: the source is contiguous
+// along a as well (a == b case, b is then another leg), so reads run along a.
 template <int PREC>
 __global__ void __launch_bounds__(256) permute_tile_kernel(const double* __restrict__ src, void* dst, int64_t plane,
-                                                           const __grid_constant__ PermuteArgs p) {
+                                                           const __grid_constant__ PermuteArgs p, int read_a_fast) {
   __shared__ double tile[2048 + 64];  // nb * TA * (TB + 1) <= 1024 (1 + 1/TB)
   __shared__ int64_t s_src[64], s_dst[64];
+  __shared__ int s_alim[64], s_blim[64];
   const int TA = int(p.da < 32 ? p.da : 32), TB = int(p.db < 32 ? p.db : 32);
   const int per_tile = TA * TB;
   const int nb = 1024 / per_tile < 64 ? 1024 / per_tile : 64;  // tiles per pass
   const int64_t ca = (p.da + TA - 1) / TA, cb = (p.db + TB - 1) / TB;
   const int64_t total = p.outer * ca * cb;
   const int tid = threadIdx.x;
+  // in-tile coordinates of this thread's (up to 4) elements
+  int rd_a[4], rd_b[4], wr_a[4], wr_b[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = tid + 256 * q;
+    if (read_a_fast) {
+      rd_b[q] = r / TA;
+      rd_a[q] = r - rd_b[q] * TA;
+    } else {
+      rd_a[q] = r / TB;
+      rd_b[q] = r - rd_a[q] * TB;
+    }
+    wr_b[q] = r / TA;
+    wr_a[q] = r - wr_b[q] * TA;
+  }
   for (int64_t t0 = int64_t(blockIdx.x) * nb; t0 < total; t0 += int64_t(gridDim.x) * nb) {
-    if (tid < nb && t0 + tid < total) {
+    const int ntiles = int(total - t0 < nb ? total - t0 : nb);
+    if (tid < ntiles) {
       const int64_t t = t0 + tid;
       const int64_t o = t / (ca * cb);
       const int64_t rem = t - o * ca * cb;
@@ -61,48 +82,35 @@ __global__ void __launch_bounds__(256) permute_tile_kernel(const double* __restr
       decode_other(p, o, so, dof);
       s_src[tid] = so + a0 * p.a_src + b0 * p.b_src;
       s_dst[tid] = dof + a0 * p.a_dst + b0 * p.b_dst;
+      s_alim[tid] = int(p.da - a0 < TA ? p.da - a0 : TA);
+      s_blim[tid] = int(p.db - b0 < TB ? p.db - b0 : TB);
     }
     __syncthreads();
-    const int ntiles = int(total - t0 < nb ? total - t0 : nb);
-    // read along b (contiguous in the source)
-    for (int e = tid; e < ntiles * per_tile; e += 256) {
-      const int j = e / per_tile, r = e - j * per_tile;
-      const int ia = r / TB, ib = r - ia * TB;
-      const int64_t t = t0 + j;
-      const int64_t rem = t % (ca * cb);
-      const bool ok = (rem / cb) * TA + ia < p.da && (rem % cb) * TB + ib < p.db;
-      tile[j * TA * (TB + 1) + ia * (TB + 1) + ib] = ok ? src[s_src[j] + ia * p.a_src + ib * p.b_src] : 0.0;
+    for (int j = 0; j < ntiles; ++j) {
+      const int64_t base = s_src[j];
+      const int alim = s_alim[j], blim = s_blim[j];
+      double* tj = tile + j * TA * (TB + 1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (tid + 256 * q >= per_tile) break;
+        const int ia = rd_a[q], ib = rd_b[q];
+        if (ia < alim && ib < blim) tj[ia * (TB + 1) + ib] = src[base + ia * p.a_src + ib * p.b_src];
+      }
     }
     __syncthreads();
-    // write along a (contiguous in the destination)
-    for (int e = tid; e < ntiles * per_tile; e += 256) {
-      const int j = e / per_tile, r = e - j * per_tile;
-      const int ib = r / TA, ia = r - ib * TA;
-      const int64_t t = t0 + j;
-      const int64_t rem = t % (ca * cb);
-      if ((rem / cb) * TA + ia < p.da && (rem % cb) * TB + ib < p.db)
-        OperandStore<PREC>::store(dst, s_dst[j] + ib * p.b_dst + ia * p.a_dst, plane,
-                                  tile[j * TA * (TB + 1) + ia * (TB + 1) + ib]);
+    for (int j = 0; j < ntiles; ++j) {
+      const int64_t base = s_dst[j];
+      const int alim = s_alim[j], blim = s_blim[j];
+      const double* tj = tile + j * TA * (TB + 1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (tid + 256 * q >= per_tile) break;
+        const int ia = wr_a[q], ib = wr_b[q];
+        if (ia < alim && ib < blim)
+          OperandStore<PREC>::store(dst, base + ib * p.b_dst + ia * p.a_dst, plane, tj[ia * (TB + 1) + ib]);
+      }
     }
     __syncthreads();
-  }
-}
-
-// a == b: lines along the common contiguous leg (size da), one warp per line chunk.
-template <int PREC>
-__global__ void __launch_bounds__(256) permute_line_kernel(const double* __restrict__ src, void* dst, int64_t plane,
-                                                           const __grid_constant__ PermuteArgs p) {
-  const int64_t chunks = (p.da + 31) / 32;
-  const int64_t total = p.outer * chunks;
-  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32;
-  const int64_t nwarps = int64_t(gridDim.x) * blockDim.x / 32;
-  const int lane = threadIdx.x % 32;
-  for (int64_t t = warp; t < total; t += nwarps) {
-    const int64_t o = t / chunks;
-    const int64_t i = (t - o * chunks) * 32 + lane;
-    int64_t so, dof;
-    decode_other(p, o, so, dof);
-    if (i < p.da) OperandStore<PREC>::store(dst, dof + i * p.a_dst, plane, src[so + i * p.a_src]);
   }
 }
 
@@ -136,13 +144,23 @@ cudaError_t launch_permute(const PermuteStep& st, const double* src, void* dst, 
     if ((ai && !aa) || (ai == aa && ds[i] < ds[a])) a = i;
     if ((ai && !(dim[b] > 1)) || (ai == (dim[b] > 1) && ss[i] < ss[b])) b = i;
   }
+  // a == b: tile over (a, b2) with b2 the leg of next-smallest source
+  // stride; reads then run along a too.  A tensor with one non-trivial leg
+  // gets a dummy b of size 1.
+  int read_a_fast = 0;
+  if (a == b) {
+    read_a_fast = 1;
+    b = -1;
+    for (int i = 0; i < n; ++i)
+      if (i != a && dim[i] > 1 && (b < 0 || ss[i] < ss[b])) b = i;
+  }
   PermuteArgs p{};
   p.da = dim[a];
-  p.db = dim[b];
+  p.db = b >= 0 ? dim[b] : 1;
   p.a_src = ss[a];
   p.a_dst = ds[a];
-  p.b_src = ss[b];
-  p.b_dst = ds[b];
+  p.b_src = b >= 0 ? ss[b] : 0;
+  p.b_dst = b >= 0 ? ds[b] : 0;
   p.outer = 1;
   // other legs, outermost first (order is irrelevant for correctness)
   for (int i = n - 1; i >= 0; --i) {
@@ -155,17 +173,11 @@ cudaError_t launch_permute(const PermuteStep& st, const double* src, void* dst, 
     ++p.n_other;
   }
   count_launch();
-  const bool line = (a == b);
-  const int64_t work = line ? p.outer * ((p.da + 31) / 32) : p.outer * ((p.da + 31) / 32) * ((p.db + 31) / 32);
   const int64_t ta = std::min<int64_t>(p.da, 32), tb = std::min<int64_t>(p.db, 32);
+  const int64_t work = p.outer * ((p.da + ta - 1) / ta) * ((p.db + tb - 1) / tb);
   const int64_t per_pass = std::min<int64_t>(std::max<int64_t>(1024 / (ta * tb), 1), 64);
-  const unsigned grid = unsigned(std::max<int64_t>(
-      1, std::min<int64_t>(line ? (work + 7) / 8 : (work + per_pass - 1) / per_pass, 152 * 16)));
-#define MERA_PERMUTE_LAUNCH(P)                                                                  \
-  if (line)                                                                                     \
-    permute_line_kernel<P><<<grid, 256, 0, stream>>>(src, dst, plane_elems, p);                \
-  else                                                                                          \
-    permute_tile_kernel<P><<<grid, 256, 0, stream>>>(src, dst, plane_elems, p);
+  const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>((work + per_pass - 1) / per_pass, 152 * 16)));
+#define MERA_PERMUTE_LAUNCH(P) permute_tile_kernel<P><<<grid, 256, 0, stream>>>(src, dst, plane_elems, p, read_a_fast);
   switch (prec) {
     case PREC_F64: MERA_PERMUTE_LAUNCH(PREC_F64) break;
     case PREC_TF32: MERA_PERMUTE_LAUNCH(PREC_TF32) break;

@@ -22,6 +22,20 @@ __device__ __forceinline__ int64_t legmap_offset(const LegMap& m, int64_t idx) {
   return off;
 }
 
+// Same, for indices below 2^31 (every GEMM row/column index; M, N < 2^31 is
+// checked at launch): 32-bit division is several times cheaper.
+__device__ __forceinline__ int64_t legmap_offset32(const LegMap& m, uint32_t idx) {
+  int64_t off = 0;
+#pragma unroll 1
+  for (int i = m.n - 1; i >= 0; --i) {
+    const uint32_t d = uint32_t(m.dim[i]);
+    const uint32_t q = idx / d;
+    off += int64_t(idx - q * d) * m.stride[i];
+    idx = q;
+  }
+  return off;
+}
+
 // Round a float to TF32 (10 explicit mantissa bits), nearest, ties away.
 __device__ __forceinline__ float round_tf32(float x) {
   uint32_t r;
@@ -41,39 +55,44 @@ struct OperandStore<PREC_F64> {
     static_cast<double*>(base)[off] = v;
   }
 };
+// The reduced-precision stores convert binary64 -> binary32 once and split in
+// FP32: GB300's FP64 pipe is ~1/1800 of its BF16 tensor rate, so every extra
+// binary64 operation per element shows up directly in the copy time.  FP32
+// keeps 24 significant bits, more than any of these operand formats holds.
 template <>
 struct OperandStore<PREC_TF32> {
   using T = float;
   __device__ __forceinline__ static void store(void* base, int64_t off, int64_t, double v) {
-    static_cast<float*>(base)[off] = round_tf32(float(v));
+    static_cast<float*>(base)[off] = round_tf32(__double2float_rn(v));
   }
 };
 template <>
 struct OperandStore<PREC_BF16> {
   using T = __nv_bfloat16;
   __device__ __forceinline__ static void store(void* base, int64_t off, int64_t, double v) {
-    static_cast<__nv_bfloat16*>(base)[off] = __double2bfloat16(v);
+    static_cast<__nv_bfloat16*>(base)[off] = __float2bfloat16_rn(__double2float_rn(v));
   }
 };
 template <>
 struct OperandStore<PREC_BF16X3> {
   using T = __nv_bfloat16;
   __device__ __forceinline__ static void store(void* base, int64_t off, int64_t plane, double v) {
-    const __nv_bfloat16 hi = __double2bfloat16(v);
-    const __nv_bfloat16 lo = __double2bfloat16(v - double(__bfloat162float(hi)));
+    const float f = __double2float_rn(v);
+    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
     static_cast<__nv_bfloat16*>(base)[off] = hi;
     static_cast<__nv_bfloat16*>(base)[off + plane] = lo;
   }
 };
-
 template <>
 struct OperandStore<PREC_BF16X6> {
   using T = __nv_bfloat16;
   __device__ __forceinline__ static void store(void* base, int64_t off, int64_t plane, double v) {
-    const __nv_bfloat16 hi = __double2bfloat16(v);
-    const double r1 = v - double(__bfloat162float(hi));
-    const __nv_bfloat16 mid = __double2bfloat16(r1);
-    const __nv_bfloat16 lo = __double2bfloat16(r1 - double(__bfloat162float(mid)));
+    const float f = __double2float_rn(v);
+    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+    const float r1 = f - __bfloat162float(hi);
+    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
     __nv_bfloat16* b = static_cast<__nv_bfloat16*>(base);
     b[off] = hi;
     b[off + plane] = mid;

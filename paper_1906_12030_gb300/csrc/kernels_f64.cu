@@ -270,10 +270,10 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const __grid_constant__ G
   for (int t = tid; t < 2 * R; t += 256) {
     if (t < R) {
       const int64_t gm = m0 + t;
-      offm[t] = gm < p.M ? legmap_offset(p.m_dst, gm) : 0;
+      offm[t] = gm < p.M ? legmap_offset32(p.m_dst, uint32_t(gm)) : 0;
     } else {
       const int64_t gn = n0 + t - R;
-      offn[t - R] = gn < p.N ? legmap_offset(p.n_dst, gn) : 0;
+      offn[t - R] = gn < p.N ? legmap_offset32(p.n_dst, uint32_t(gn)) : 0;
     }
   }
   __syncthreads();
@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const __grid_constant__ G
 
 cudaError_t launch_gemm_f64(const GemmF64Args& args, cudaStream_t stream) {
   if (args.M <= 0 || args.N <= 0) return cudaSuccess;
+  if (args.M > 0x7fffffff || args.N > 0x7fffffff) return cudaErrorInvalidValue;  // 32-bit row/column decode
   auto tiles = [&](int64_t r) { return ((args.M + r - 1) / r) * ((args.N + r - 1) / r); };
   constexpr int64_t kFill = 2 * 152;  // enough blocks to occupy every SM twice
   count_launch();

@@ -325,13 +325,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (et == 0) *abort_snapshot = *abort_flag;
       for (int c = et; c < BN; c += 128) {
         const int64_t n = n0 + c;
-        off_n[c] = n < ep.N ? legmap_offset(ep.n_dst, n) : 0;
+        off_n[c] = n < ep.N ? legmap_offset32(ep.n_dst, uint32_t(n)) : 0;
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (*abort_snapshot) break;
       const int64_t m = m0 + row;
       const bool row_ok = m < ep.M;
-      const int64_t off_m = row_ok ? legmap_offset(ep.m_dst, m) : 0;
+      const int64_t off_m = row_ok ? legmap_offset32(ep.m_dst, uint32_t(m)) : 0;
       const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], (tc >> 1) & 1, abort_flag) ? 1 : 0);
       tc_fence_after();
       if (!ok) continue;  // the next snapshot sees the abort flag
@@ -405,14 +405,14 @@ template <int PREC>
 __global__ void __launch_bounds__(256) splitk_reduce_kernel(const __grid_constant__ Epilogue ep) {
   const int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (m >= ep.M) return;
-  const int64_t off_m = legmap_offset(ep.m_dst, m);
+  const int64_t off_m = legmap_offset32(ep.m_dst, uint32_t(m));
   const int64_t n_per = (ep.N + gridDim.y - 1) / gridDim.y;
   const int64_t n_lo = int64_t(blockIdx.y) * n_per, n_hi = min(ep.N, n_lo + n_per);
   for (int64_t n = n_lo; n < n_hi; ++n) {
     double acc = 0.0;
     for (int s = 0; s < ep.split; ++s) acc += double(ep.partial[(int64_t(s) * ep.N + n) * ep.M + m]);
     const double val = ep.alpha * acc;
-    const int64_t off = off_m + legmap_offset(ep.n_dst, n);
+    const int64_t off = off_m + legmap_offset32(ep.n_dst, uint32_t(n));
     if (ep.c_final) {
       double* dst = static_cast<double*>(ep.C) + off;
       *dst = ep.accumulate ? (*dst + val) : val;

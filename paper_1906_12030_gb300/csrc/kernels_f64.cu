@@ -25,18 +25,22 @@ struct PermuteArgs {
   int64_t outer;           // product of the other legs' sizes
 };
 
-__device__ __forceinline__ void decode_other(const PermuteArgs& p, int64_t o, int64_t& so, int64_t& dof) {
+// o < 2^31 (checked at launch), so the decode divides in 32 bits.
+__device__ __forceinline__ void decode_other(const PermuteArgs& p, uint32_t o, int64_t& so, int64_t& dof) {
   so = 0;
   dof = 0;
 #pragma unroll 1
   for (int i = p.n_other - 1; i >= 0; --i) {
-    const int64_t q = o / p.dim[i];
-    const int64_t x = o - q * p.dim[i];
+    const uint32_t d = uint32_t(p.dim[i]);
+    const uint32_t q = o / d;
+    const int64_t x = int64_t(o - q * d);
     so += x * p.src_stride[i];
     dof += x * p.dst_stride[i];
     o = q;
   }
 }
+
+constexpr int kPermuteTile = 4352;  // doubles of shared memory per block (34.8 KB)
 
 // Tiles of TA x TB (a, b) elements, TA, TB <= 32; several tiles (consecutive
 // outer indices) per block pass so that a pass moves up to 1024 elements.
@@ -47,13 +51,14 @@ __device__ __forceinline__ void decode_other(const PermuteArgs& p, int64_t o, in
 template <int PREC>
 __global__ void __launch_bounds__(256) permute_tile_kernel(const double* __restrict__ src, void* dst, int64_t plane,
                                                            const __grid_constant__ PermuteArgs p, int read_a_fast) {
-  __shared__ double tile[2048 + 64];  // nb * TA * (TB + 1) <= 1024 (1 + 1/TB)
+  __shared__ double tile[kPermuteTile];
   __shared__ int64_t s_src[64], s_dst[64];
   __shared__ int s_alim[64], s_blim[64];
   const int TA = int(p.da < 32 ? p.da : 32), TB = int(p.db < 32 ? p.db : 32);
   const int per_tile = TA * TB;
-  const int nb = 1024 / per_tile < 64 ? 1024 / per_tile : 64;  // tiles per pass
-  const int64_t ca = (p.da + TA - 1) / TA, cb = (p.db + TB - 1) / TB;
+  const int cap = kPermuteTile / (TA * (TB + 1));
+  const int nb = cap < 64 ? cap : 64;  // tiles per pass (up to ~4096 elements)
+  const uint32_t ca = uint32_t((p.da + TA - 1) / TA), cb = uint32_t((p.db + TB - 1) / TB);
   const int64_t total = p.outer * ca * cb;
   const int tid = threadIdx.x;
   // in-tile coordinates of this thread's (up to 4) elements
@@ -74,10 +79,10 @@ __global__ void __launch_bounds__(256) permute_tile_kernel(const double* __restr
   for (int64_t t0 = int64_t(blockIdx.x) * nb; t0 < total; t0 += int64_t(gridDim.x) * nb) {
     const int ntiles = int(total - t0 < nb ? total - t0 : nb);
     if (tid < ntiles) {
-      const int64_t t = t0 + tid;
-      const int64_t o = t / (ca * cb);
-      const int64_t rem = t - o * ca * cb;
-      const int64_t a0 = (rem / cb) * TA, b0 = (rem % cb) * TB;
+      const uint32_t t = uint32_t(t0 + tid);
+      const uint32_t o = t / (ca * cb);
+      const uint32_t rem = t - o * ca * cb;
+      const int64_t a0 = int64_t(rem / cb) * TA, b0 = int64_t(rem % cb) * TB;
       int64_t so, dof;
       decode_other(p, o, so, dof);
       s_src[tid] = so + a0 * p.a_src + b0 * p.b_src;
@@ -175,7 +180,8 @@ cudaError_t launch_permute(const PermuteStep& st, const double* src, void* dst, 
   count_launch();
   const int64_t ta = std::min<int64_t>(p.da, 32), tb = std::min<int64_t>(p.db, 32);
   const int64_t work = p.outer * ((p.da + ta - 1) / ta) * ((p.db + tb - 1) / tb);
-  const int64_t per_pass = std::min<int64_t>(std::max<int64_t>(1024 / (ta * tb), 1), 64);
+  const int64_t per_pass = std::min<int64_t>(std::max<int64_t>(kPermuteTile / (ta * (tb + 1)), 1), 64);
+  if (work >= (int64_t(1) << 31)) return cudaErrorInvalidValue;  // 32-bit tile indices
   const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>((work + per_pass - 1) / per_pass, 152 * 16)));
 #define MERA_PERMUTE_LAUNCH(P) permute_tile_kernel<P><<<grid, 256, 0, stream>>>(src, dst, plane_elems, p, read_a_fast);
   switch (prec) {

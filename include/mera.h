@@ -268,6 +268,14 @@ mera_status mera_profile_enable(int on);
  */
 mera_status mera_profile_read(int kind, long long* launches, double* ms, double* flops);
 
+/*
+ * Ket/bra transpose of a 3-site operator: out[I][J] = x[J][I] with I, J the
+ * ket and bra triples of local dimension d (x, out: d^6 doubles on the
+ * device, distinct).  Used by the energy adjoint: dE/dh = D(rho^T) and
+ * dE/drho = A(h^T) for E = tr(A(h) rho) (Sec. II B).
+ */
+mera_status mera_op_transpose(const double* x, int d, double* out, void* stream);
+
 /* Bytes of the device array that backs mera_ascend_noalloc (32 MiB). */
 #define MERA_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 

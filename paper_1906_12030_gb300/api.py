@@ -20,7 +20,7 @@ __all__ = [
     "mera_energy", "mera_ising_h1", "mera_sweep", "mera_sweep_workspace_size", "mera_plan_json", "mera_flops",
     "workspace", "MeraState", "mera_launch_count", "mera_profile_enable", "mera_profile_read",
     "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE", "mera_device_status", "mera_gemm_test",
-    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES",
+    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose",
 ]
 
 PREC_F64, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3, 4
@@ -97,6 +97,7 @@ def library():
             "mera_device_status": ([ctypes.POINTER(i), i], i),
             "mera_gemm_test": ([i, vp, vp, i, i, i, vp, vp, sz, vp], i),
             "mera_ascend_noalloc": ([vp, vp, vp, i, i, vp, i, vp], i),
+            "mera_op_transpose": ([vp, i, vp, vp], i),
             "mera_profile_enable": ([i], i),
             "mera_profile_read": ([i, ctypes.POINTER(ctypes.c_longlong), pd, pd], i),
         }
@@ -354,4 +355,10 @@ def mera_ascend_noalloc(h, u, w, chi_b, chi_t, out, prec=PREC_F64, stream=None):
     _check(library().mera_ascend_noalloc(_f64(h, chi_b ** 6, "h"), _f64(u, chi_b ** 4, "u"),
                                          _f64(w, chi_b ** 2 * chi_t, "w"), chi_b, chi_t,
                                          _f64(out, chi_t ** 6, "out"), prec, _stream(stream)))
+    return out
+
+
+def mera_op_transpose(x, d, out, stream=None):
+    """out[I, J] = x[J, I] for a 3-site operator of local dimension d."""
+    _check(library().mera_op_transpose(_f64(x, d ** 6, "x"), d, _f64(out, d ** 6, "out"), _stream(stream)))
     return out

@@ -666,3 +666,16 @@ namespace mera {
 // entry points defined in other translation units.
 mera_status set_last_error(mera_status st, const char* msg) { return fail(st, "%s", msg); }
 }  // namespace mera
+
+extern "C" mera_status mera_op_transpose(const double* x, int d, double* out, void* stream) {
+  if (!x || !out || x == out) return fail(MERA_EINVAL, "bad transpose pointers");
+  if (d < 1 || d > MERA_MAX_CHI) return fail(MERA_EINVAL, "bad local dimension %d", d);
+  const int64_t n = ipow(d, 3);
+  PermuteStep st;  // out[r][c] = x[c][r]
+  st.rows = n;
+  st.cols = n;
+  st.ld = n;
+  st.row_src.n = 1; st.row_src.dim[0] = n; st.row_src.stride[0] = 1;
+  st.col_src.n = 1; st.col_src.dim[0] = n; st.col_src.stride[0] = n;
+  return cuda_status(launch_permute(st, x, out, 0, PREC_F64, static_cast<cudaStream_t>(stream)), "transpose");
+}

@@ -8,8 +8,10 @@
 //   warp 0      TMA producer (one elected lane), STAGES-deep ring shared by
 //               all of the CTA's tiles
 //   warp 1      tensor-memory allocator + MMA issuer (one lane)
-//   warps 2..5  epilogue: tcgen05.ld of the accumulator, convert, store; the
-//               accumulator is handed back to the MMA warp after its last load
+//   warps 2..9  epilogue: tcgen05.ld of the accumulator, convert, store; two
+//               warps per tensor-memory lane quarter, each taking half of the
+//               tile's columns; the accumulator is handed back to the MMA warp
+//               after the last load of all eight
 // Every mbarrier wait is bounded; a wait that gives up records
 // MERA_ETIMEOUT in a device status word, raises a CTA-wide abort flag, and
 // every role drains its copies in flight and leaves.
@@ -31,7 +33,8 @@ namespace {
 
 constexpr int kBM = 128;          // UMMA M (cta_group::1)
 constexpr int kSlabBytes = 128;   // one swizzle row: 64 BF16 or 32 TF32 along K
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
 constexpr uint64_t kTimeoutNs = 2000000000ull;  // a wait longer than 2 s is a failure
 constexpr uint32_t kSpinCap = 1u << 30;            // second bound, independent of the timer
 
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);  // one arrive per epilogue warp
+      mbar_init(&acc_empty[b], kEpiWarps);  // one arrive per epilogue warp
     }
     *abort_flag = 0;
     *abort_snapshot = 0;
@@ -309,10 +312,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---- epilogue (warps 2..5) -------------------------------------------------
-    const int et = threadIdx.x - 64;  // 0..127
+    // ---- epilogue (warps 2..9) -------------------------------------------------
+    const int et = threadIdx.x - 64;  // 0..255
     const int quarter = warp % 4;     // tensor-memory lanes this warp may read
+    const int half = (warp - 2) / 4;  // which half of the tile's 32-column chunks
     const int row = quarter * 32 + lane;
+    constexpr int kChunks = BN < 32 ? 1 : BN / 32;
+    const int ch_lo = kChunks == 1 ? (half == 0 ? 0 : 1) : half * (kChunks / 2);
+    const int ch_hi = kChunks == 1 ? 1 : (half + 1) * (kChunks / 2);
     const float alpha = float(ep.alpha);
     uint32_t tc = 0;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++tc) {
@@ -321,13 +328,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t b = tc & 1;
       // all epilogue threads are done with the previous tile's off_n; decide
       // together whether to go on
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, 256;" ::: "memory");
       if (et == 0) *abort_snapshot = *abort_flag;
-      for (int c = et; c < BN; c += 128) {
+      for (int c = et; c < BN; c += 256) {
         const int64_t n = n0 + c;
         off_n[c] = n < ep.N ? legmap_offset32(ep.n_dst, uint32_t(n)) : 0;
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, 256;" ::: "memory");
       if (*abort_snapshot) break;
       const int64_t m = m0 + row;
       const bool row_ok = m < ep.M;
@@ -336,11 +343,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       if (!ok) continue;  // the next snapshot sees the abort flag
       const uint32_t taddr = tmem + b * uint32_t(C::kAccCols) + (uint32_t(quarter * 32) << 16);
+      if (ch_lo >= ch_hi) {  // no columns for this warp: hand the accumulator back at once
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[b]);
+        continue;
+      }
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int ch = ch_lo; ch < ch_hi; ++ch) {
+        const int c0 = ch * 32;
         uint32_t v[32];
         tmem_ld32(taddr + uint32_t(c0), v);
-        if (c0 + 32 >= BN) {  // last read of this accumulator: hand it back
+        if (ch + 1 == ch_hi) {  // this warp's last read of the accumulator: hand it back
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&acc_empty[b]);

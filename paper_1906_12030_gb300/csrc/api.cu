@@ -127,13 +127,16 @@ struct Arena {
 };
 
 // Execute a contraction program; inputs[slot] are device pointers.
+// reuse_resident: the u/w operand copies left by the previous run of this
+// same program (same u, w, workspace) are still valid; skip those copies.
 mera_status run_program(const OpProgram& prog, const double* const inputs[4], double* out, int prec, char* ws,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, bool reuse_resident = false) {
   for (const Program& dg : prog.diagrams) {
     for (const Step& st : dg.steps) {
       if (st.kind == 0) {
         const PermuteStep& p = st.p;
         const Buffer& b = dg.bufs[p.dst_buf];
+        if (reuse_resident && b.resident) continue;
         const int64_t plane = b.plane_bytes / elem_bytes(prec);
         ProfScope ps(stream, 1, 0, 0.0);
         cudaError_t e = launch_permute(p, inputs[p.slot], ws + b.offset, plane, prec, stream);
@@ -321,7 +324,8 @@ extern "C" mera_status mera_fixed_point_rho(const double* u, const double* w, in
   double* scalars = red + 4096;
   const double* inputs[4] = {nullptr, rho_inout, u, w};
   for (int it = 0; it < n_iter; ++it) {
-    st = run_program(*prog, inputs, tmp, prec, pws, s);
+    // u and w are fixed during the iteration: their operand copies are made once
+    st = run_program(*prog, inputs, tmp, prec, pws, s, it > 0);
     if (st != MERA_OK) return st;
     cudaError_t e = launch_sym_normalize(tmp, rho_inout, n, red, scalars, resid_dev, s);
     if (e != cudaSuccess) return cuda_status(e, "sym_normalize");

@@ -61,21 +61,7 @@ __global__ void __launch_bounds__(256) permute_tile_kernel(const double* __restr
   const uint32_t ca = uint32_t((p.da + TA - 1) / TA), cb = uint32_t((p.db + TB - 1) / TB);
   const int64_t total = p.outer * ca * cb;
   const int tid = threadIdx.x;
-  // in-tile coordinates of this thread's (up to 4) elements
-  int rd_a[4], rd_b[4], wr_a[4], wr_b[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int r = tid + 256 * q;
-    if (read_a_fast) {
-      rd_b[q] = r / TA;
-      rd_a[q] = r - rd_b[q] * TA;
-    } else {
-      rd_a[q] = r / TB;
-      rd_b[q] = r - rd_a[q] * TB;
-    }
-    wr_b[q] = r / TA;
-    wr_a[q] = r - wr_b[q] * TA;
-  }
+  const int tstride = TA * (TB + 1);
   for (int64_t t0 = int64_t(blockIdx.x) * nb; t0 < total; t0 += int64_t(gridDim.x) * nb) {
     const int ntiles = int(total - t0 < nb ? total - t0 : nb);
     if (tid < ntiles) {
@@ -91,29 +77,44 @@ __global__ void __launch_bounds__(256) permute_tile_kernel(const double* __restr
       s_blim[tid] = int(p.db - b0 < TB ? p.db - b0 : TB);
     }
     __syncthreads();
-    for (int j = 0; j < ntiles; ++j) {
-      const int64_t base = s_src[j];
-      const int alim = s_alim[j], blim = s_blim[j];
-      double* tj = tile + j * TA * (TB + 1);
+    const int count = ntiles * per_tile;
+    // reads: 8 independent loads per thread in flight before any shared store
+    for (int e0 = 0; e0 < count; e0 += 256 * 8) {
+      double v[8];
+      int slot[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (tid + 256 * q >= per_tile) break;
-        const int ia = rd_a[q], ib = rd_b[q];
-        if (ia < alim && ib < blim) tj[ia * (TB + 1) + ib] = src[base + ia * p.a_src + ib * p.b_src];
+      for (int k = 0; k < 8; ++k) {
+        const int e = e0 + tid + 256 * k;
+        slot[k] = -1;
+        v[k] = 0.0;
+        if (e < count) {
+          const int j = e / per_tile, r = e - j * per_tile;
+          int ia, ib;
+          if (read_a_fast) {
+            ib = r / TA;
+            ia = r - ib * TA;
+          } else {
+            ia = r / TB;
+            ib = r - ia * TB;
+          }
+          if (ia < s_alim[j] && ib < s_blim[j]) {
+            v[k] = src[s_src[j] + ia * p.a_src + ib * p.b_src];
+            slot[k] = j * tstride + ia * (TB + 1) + ib;
+          }
+        }
       }
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (slot[k] >= 0) tile[slot[k]] = v[k];
     }
     __syncthreads();
-    for (int j = 0; j < ntiles; ++j) {
-      const int64_t base = s_dst[j];
-      const int alim = s_alim[j], blim = s_blim[j];
-      const double* tj = tile + j * TA * (TB + 1);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (tid + 256 * q >= per_tile) break;
-        const int ia = wr_a[q], ib = wr_b[q];
-        if (ia < alim && ib < blim)
-          OperandStore<PREC>::store(dst, base + ib * p.b_dst + ia * p.a_dst, plane, tj[ia * (TB + 1) + ib]);
-      }
+    // writes along a (contiguous in the destination)
+    for (int e = tid; e < count; e += 256) {
+      const int j = e / per_tile, r = e - j * per_tile;
+      const int ib = r / TA, ia = r - ib * TA;
+      if (ia < s_alim[j] && ib < s_blim[j])
+        OperandStore<PREC>::store(dst, s_dst[j] + ib * p.b_dst + ia * p.a_dst, plane,
+                                  tile[j * tstride + ia * (TB + 1) + ib]);
     }
     __syncthreads();
   }

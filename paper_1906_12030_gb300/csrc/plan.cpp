@@ -409,6 +409,7 @@ struct Builder {
         prog.steps.push_back(s);
         const int si = int(prog.steps.size()) - 1;
         first_use[p.dst_buf] = si;
+        if (ts.slot == SLOT_U || ts.slot == SLOT_W) prog.bufs[p.dst_buf].resident = 1;
         continue;
       }
       const G& gi = g[i];
@@ -468,12 +469,24 @@ struct Builder {
       if (st.kind == 1) fmax = std::max(fmax, st.g.flops);
     for (Step& st : prog.steps)
       if (st.kind == 1) st.g.dominant = st.g.flops >= 0.25 * fmax;
+    // Resident buffers (operand copies of u and w) are packed one after the
+    // other and never reused, so a caller may run the program again with the
+    // same u and w without repeating those copies.  Offsets here are
+    // relative to the resident region; get_program adds its base.
+    size_t res_top = 0;
+    for (Buffer& b : prog.bufs)
+      if (b.resident) {
+        b.offset = int64_t(res_top);
+        res_top += size_t(b.bytes);
+      }
+    prog.resident_bytes = res_top;
     // Arena: first-fit over [first_use, last_use] intervals.
     struct Iv { int64_t off, bytes; int lo, hi; };
     std::vector<Iv> placed;
     size_t top = 0;
     for (size_t bi = 0; bi < prog.bufs.size(); ++bi) {
       Buffer& b = prog.bufs[bi];
+      if (b.resident) continue;
       const int lo = first_use[bi], hi = last_use[bi];
       std::vector<std::pair<int64_t, int64_t>> busy;
       for (auto& iv : placed)
@@ -522,10 +535,23 @@ const OpProgram* get_program(int op, int chi_b, int chi_t, int prec) {
   for (size_t d = 0; d < ds.size(); ++d) {
     Builder b(ds[d], dim, prec, 0.5, d == 0 ? 0 : 1);
     if (!b.build()) return nullptr;
-    prog->ws_bytes = std::max(prog->ws_bytes, b.prog.ws_bytes);
     prog->flops += b.prog.flops;
     prog->diagrams.push_back(std::move(b.prog));
   }
+  // Workspace: [resident copies of diagram 0 | diagram 1 | ...][transient arena]
+  size_t res_base = 0;
+  for (Program& pg : prog->diagrams) {
+    for (Buffer& bf : pg.bufs)
+      if (bf.resident) bf.offset += int64_t(res_base);
+    res_base += (pg.resident_bytes + 255) / 256 * 256;
+  }
+  size_t trans = 0;
+  for (Program& pg : prog->diagrams) {
+    for (Buffer& bf : pg.bufs)
+      if (!bf.resident) bf.offset += int64_t(res_base);
+    trans = std::max(trans, pg.ws_bytes);
+  }
+  prog->ws_bytes = res_base + trans;
   const OpProgram* out = prog.get();
   g_cache[k] = std::move(prog);
   return out;
@@ -549,7 +575,8 @@ std::string program_json(const OpProgram& prog, int op, int chi_b, int chi_t, in
     o << (d ? "," : "") << "{\"ws_bytes\":" << p.ws_bytes << ",\"flops\":" << p.flops << ",\"bufs\":[";
     for (size_t b = 0; b < p.bufs.size(); ++b)
       o << (b ? "," : "") << "{\"rows\":" << p.bufs[b].rows << ",\"ld\":" << p.bufs[b].ld
-        << ",\"offset\":" << p.bufs[b].offset << ",\"bytes\":" << p.bufs[b].bytes << "}";
+        << ",\"offset\":" << p.bufs[b].offset << ",\"bytes\":" << p.bufs[b].bytes
+        << ",\"resident\":" << p.bufs[b].resident << "}";
     o << "],\"steps\":[";
     for (size_t s = 0; s < p.steps.size(); ++s) {
       const Step& st = p.steps[s];

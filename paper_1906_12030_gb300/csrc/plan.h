@@ -68,13 +68,15 @@ struct Buffer {
   int64_t offset = 0;         // byte offset in the workspace
   int64_t plane_bytes = 0;    // bytes of one plane (BF16X3 keeps hi, then lo)
   int64_t bytes = 0;          // plane_bytes * planes
+  int resident = 0;           // copy of a disentangler/isometry: kept for the whole call
 };
 
 // The program of one diagram.  Buffers are laid out in one arena.
 struct Program {
   std::vector<Step> steps;
   std::vector<Buffer> bufs;
-  size_t ws_bytes = 0;
+  size_t ws_bytes = 0;        // transient arena bytes (resident buffers excluded)
+  size_t resident_bytes = 0;  // bytes of the resident buffers
   double flops = 0.0;
   int out_rank = 0;
 };

@@ -192,3 +192,22 @@ def test_split_k_partials_do_not_overlap_live_buffers():
             for other in (st["a_buf"], st["b_buf"]) + ((st["c_buf"],) if st["c_buf"] >= 0 else ()):
                 o = bufs[other]
                 assert p["offset"] + p["bytes"] <= o["offset"] or o["offset"] + o["bytes"] <= p["offset"]
+
+
+@pytest.mark.parametrize("op", [m.OP_DESCEND, m.OP_ENV_W])
+def test_resident_operand_copies_are_never_reused(op):
+    """The operand copies of u and w are kept for the whole call (the fixed
+    point reuses them across its power steps): they must not overlap each
+    other, in any diagram, nor any transient buffer."""
+    plan = m.mera_plan_json(op, 4, 4, m.PREC_BF16X3)
+    resident, transient = [], []
+    for dg in plan["diagrams"]:
+        for b in dg["bufs"]:
+            (resident if b["resident"] else transient).append((b["offset"], b["offset"] + b["bytes"]))
+    assert resident
+    resident.sort()
+    for (a0, a1), (b0, b1) in zip(resident, resident[1:]):
+        assert a1 <= b0
+    for r0, r1 in resident:
+        for t0, t1 in transient:
+            assert r1 <= t0 or t1 <= r0

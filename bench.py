@@ -36,7 +36,7 @@ HZ = 1.0
 SEED = 0
 # nominal dense tensor/FP64 rates (PFLOP/s) used only to carry the measured
 # BF16 peak over to the other dtypes
-NOMINAL = {"bf16": 2.25, "tf32": 1.1, "f64": 0.00125, "bf16x3": 2.25 / 3.0}
+NOMINAL = {"bf16": 2.25, "tf32": 1.1, "f64": 0.00125, "bf16x3": 2.25 / 3.0, "bf16x6": 2.25 / 6.0}
 
 
 def _args():
@@ -46,7 +46,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--chi", type=int, default=16)
-    ap.add_argument("--prec", default="bf16x3", choices=["f64", "tf32", "bf16", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x3", choices=["f64", "tf32", "bf16", "bf16x3", "bf16x6"])
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed FP64 sweeps (after one untimed) for the mixed-vs-FP64 comparison; 0 skips it")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -119,3 +119,38 @@ def test_fixed_point_and_energy_mixed(prec):
     rm = r.reshape(chi ** 3, -1)
     assert abs(np.trace(rm) - 1.0) < 1e-14
     assert np.abs(rm - rm.T).max() == 0.0
+
+
+# --------------------------------------------------------------------------
+# The benchmarked configuration: chi = 16 in BF16X3 (bench.py's default).
+# Sampled rows against the oracle's row-by-row contraction, and properties
+# that hold at any size.
+# --------------------------------------------------------------------------
+def test_chi16_bf16x3_sampled_rows_and_properties():
+    chi, prec = 16, m.PREC_BF16X3
+    rng = np.random.default_rng(90)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    h, rho = I.random_operator(rng, chi), I.random_density(rng, chi)
+    d = lambda x: _cuda(x).reshape(-1)  # noqa: E731
+    ud, wd, hd, rd = d(u), d(w), d(h), d(rho)
+    a = torch.empty(chi ** 6, dtype=torch.float64, device="cuda")
+    m.mera_ascend(hd, ud, wd, chi, chi, a, prec=prec)
+    got = a.cpu().numpy().reshape((chi,) * 6)
+    rows = [(0, 0, 0), (5, 11, 2), (15, 15, 15)]
+    want = O.ascend_rows(h, u, w, rows)
+    scale = np.abs(want).max()
+    for k, (p, q, r) in enumerate(rows):
+        assert np.abs(got[p, q, r] - want[k]).max() <= MAP_TOL[prec] * scale
+    # duality of the GPU maps themselves, and trace preservation of D
+    dd = torch.empty(chi ** 6, dtype=torch.float64, device="cuda")
+    m.mera_descend(rd, ud, wd, chi, chi, dd, prec=prec)
+    lhs = float(torch.dot(a, rd))
+    rhs = float(torch.dot(hd, dd))
+    assert abs(lhs - rhs) <= MAP_TOL[prec] * (abs(lhs) + 1e-30) * 10
+    tr = float(torch.trace(dd.reshape(chi ** 3, chi ** 3)))
+    assert tr == pytest.approx(1.0, abs=MAP_TOL[prec])
+    # A(1) = 1 (Eq. iso, Eq. unitarity)
+    eye = torch.eye(chi ** 3, dtype=torch.float64, device="cuda").reshape(-1)
+    m.mera_ascend(eye, ud, wd, chi, chi, a, prec=prec)
+    err = (a.reshape(chi ** 3, chi ** 3) - torch.eye(chi ** 3, dtype=torch.float64, device="cuda")).abs().max()
+    assert float(err) < MAP_TOL[prec]

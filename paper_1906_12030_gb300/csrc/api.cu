@@ -327,7 +327,8 @@ extern "C" mera_status mera_fixed_point_rho(const double* u, const double* w, in
     // u and w are fixed during the iteration: their operand copies are made once
     st = run_program(*prog, inputs, tmp, prec, pws, s, it > 0);
     if (st != MERA_OK) return st;
-    cudaError_t e = launch_sym_normalize(tmp, rho_inout, n, red, scalars, resid_dev, s);
+    // the residual is reported for the last step only
+    cudaError_t e = launch_sym_normalize(tmp, rho_inout, n, red, scalars, it + 1 == n_iter ? resid_dev : nullptr, s);
     if (e != cudaSuccess) return cuda_status(e, "sym_normalize");
   }
   return MERA_OK;

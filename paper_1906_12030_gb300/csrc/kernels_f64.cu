@@ -78,6 +78,9 @@ __global__ void __launch_bounds__(256) permute_tile_kernel(const double* __restr
     }
     __syncthreads();
     const int count = ntiles * per_tile;
+    // x / d for x <= 2^22 by a float reciprocal: (x + 0.5) / d is at least
+    // 0.5 / d away from an integer, far more than the float rounding error
+    const float inv_pt = 1.0f / float(per_tile), inv_ta = 1.0f / float(TA), inv_tb = 1.0f / float(TB);
     // reads: 8 independent loads per thread in flight before any shared store
     for (int e0 = 0; e0 < count; e0 += 256 * 8) {
       double v[8];
@@ -88,13 +91,13 @@ __global__ void __launch_bounds__(256) permute_tile_kernel(const double* __restr
         slot[k] = -1;
         v[k] = 0.0;
         if (e < count) {
-          const int j = e / per_tile, r = e - j * per_tile;
+          const int j = int((float(e) + 0.5f) * inv_pt), r = e - j * per_tile;
           int ia, ib;
           if (read_a_fast) {
-            ib = r / TA;
+            ib = int((float(r) + 0.5f) * inv_ta);
             ia = r - ib * TA;
           } else {
-            ia = r / TB;
+            ia = int((float(r) + 0.5f) * inv_tb);
             ib = r - ia * TB;
           }
           if (ia < s_alim[j] && ib < s_blim[j]) {
@@ -110,8 +113,8 @@ __global__ void __launch_bounds__(256) permute_tile_kernel(const double* __restr
     __syncthreads();
     // writes along a (contiguous in the destination)
     for (int e = tid; e < count; e += 256) {
-      const int j = e / per_tile, r = e - j * per_tile;
-      const int ib = r / TA, ia = r - ib * TA;
+      const int j = int((float(e) + 0.5f) * inv_pt), r = e - j * per_tile;
+      const int ib = int((float(r) + 0.5f) * inv_ta), ia = r - ib * TA;
       if (ia < s_alim[j] && ib < s_blim[j])
         OperandStore<PREC>::store(dst, s_dst[j] + ib * p.b_dst + ia * p.a_dst, plane,
                                   tile[j * tstride + ia * (TB + 1) + ib]);
@@ -403,6 +406,7 @@ __global__ void __launch_bounds__(1024) trace_kernel(const double* __restrict__ 
   if (threadIdx.x == 0) *out = v;
 }
 
+template <bool RESID>
 __global__ void __launch_bounds__(256) sym_normalize_kernel(const double* __restrict__ X, double* rho, int64_t n,
                                                             const double* __restrict__ trace, double* partials) {
   __shared__ double xt[32][33];
@@ -420,34 +424,43 @@ __global__ void __launch_bounds__(256) sym_normalize_kernel(const double* __rest
       const int64_t gi = i0 + r, gj = j0 + threadIdx.x;
       if (gi < n && gj < n) {
         const double nv = (X[gi * n + gj] + xt[r][threadIdx.x]) * inv2t;
-        const double d = nv - rho[gi * n + gj];
-        v += d * d;
+        if constexpr (RESID) {
+          const double d = nv - rho[gi * n + gj];
+          v += d * d;
+        }
         rho[gi * n + gj] = nv;
       }
     }
     __syncthreads();
   }
-  __shared__ double sh[8];
-  double s = v;
+  if constexpr (RESID) {
+    __shared__ double sh[8];
+    double s = v;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (threadIdx.x == 0) sh[threadIdx.y] = s;
-  __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < 8; ++w) tot += sh[w];
-    partials[blockIdx.x] = tot;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) sh[threadIdx.y] = s;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < 8; ++w) tot += sh[w];
+      partials[blockIdx.x] = tot;
+    }
   }
 }
 
 cudaError_t launch_sym_normalize(const double* X, double* rho, int64_t n, double* partials, double* scalars,
                                  double* resid, cudaStream_t stream) {
-  count_launch(3);
   trace_kernel<<<1, 1024, 0, stream>>>(X, n, scalars);
   const int64_t nt = (n + 31) / 32;
   const int nb = reduction_blocks(nt * nt);
-  sym_normalize_kernel<<<nb, dim3(32, 8), 0, stream>>>(X, rho, n, scalars, partials);
-  reduce_partials_kernel<<<1, 1024, 0, stream>>>(partials, nb, resid ? resid : scalars + 1, 1);
+  if (resid) {
+    count_launch(3);
+    sym_normalize_kernel<true><<<nb, dim3(32, 8), 0, stream>>>(X, rho, n, scalars, partials);
+    reduce_partials_kernel<<<1, 1024, 0, stream>>>(partials, nb, resid, 1);
+  } else {
+    count_launch(2);
+    sym_normalize_kernel<false><<<nb, dim3(32, 8), 0, stream>>>(X, rho, n, scalars, partials);
+  }
   return cudaGetLastError();
 }
 

@@ -51,7 +51,7 @@ def _args():
                     help="timed FP64 sweeps (after one untimed) for the mixed-vs-FP64 comparison; 0 skips it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--case", default="sweep", choices=["sweep", "ascend", "descend", "env_u", "env_w"],
+    ap.add_argument("--case", default="sweep", choices=["sweep", "ascend", "descend", "env_u", "env_w", "batch"],
                     help="sweep: the benchmark; otherwise time one map call (after one warm call), for profiling")
     return ap.parse_args()
 
@@ -421,8 +421,78 @@ def run_case(args):
                       "gemm_ms": allg[1], "permute_ms": perm[1], "device_status": m.mera_device_status()}), flush=True)
 
 
+def run_batch(args):
+    """Batching: 32 independent MERAs, h ~ U[0.9, 1.1], chi from {8, 12, 16}
+    (seeded), one sweep each per step; one-at-a-time vs mera_sweep_batch."""
+    import numpy as np
+    import torch
+
+    import mera_inputs as I
+    import paper_1906_12030_gb300 as m
+
+    prec = m.PRECS[args.prec]
+    rng = np.random.default_rng(SEED)
+    specs = [(s, int(rng.choice([8, 12, 16])), float(rng.uniform(0.9, 1.1))) for s in range(32)]
+
+    def make():
+        out = []
+        for seed, chi, hz in specs:
+            layers = I.init_mera(seed, chi)
+            us = [torch.from_numpy(u).cuda().reshape(-1).contiguous() for u, _ in layers]
+            ws_ = [torch.from_numpy(w).cuda().contiguous() for _, w in layers]
+            rho = (torch.eye(chi ** 3, dtype=torch.float64, device="cuda") / chi ** 3).reshape(-1).contiguous()
+            h1, shift = m.mera_ising_h1(hz)
+            st = m.MeraState(us, ws_, rho)
+            wsb = m.workspace(m.mera_sweep_workspace_size(st.chi_b, st.chi_t, prec))
+            out.append((st, torch.from_numpy(h1.reshape(-1)).cuda(), shift, wsb))
+        return out
+
+    flops = sum(_sweep_flops(m, chi) for _, chi, _ in specs)
+    res = {}
+    for mode in ("one_at_a_time", "batched"):
+        ms = make()
+        e = torch.empty(len(ms), dtype=torch.float64, device="cuda")
+        streams = [torch.cuda.Stream() for _ in ms]
+
+        def step():
+            if mode == "batched":
+                try:
+                    m.mera_sweep_batch([x[0] for x in ms], [x[1] for x in ms], [x[2] for x in ms], N_POW, e,
+                                       prec=prec, wss=[x[3] for x in ms], streams=streams, n_threads=16)
+                except m.MeraNotConverged:
+                    pass
+            else:
+                for i, (st, h1, shift, wsb) in enumerate(ms):
+                    try:
+                        m.mera_sweep(st, h1, shift, N_POW, e[i:i + 1], prec=prec, ws=wsb)
+                    except m.MeraNotConverged:
+                        pass
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        res[mode] = {"mera_sweeps_per_s": len(ms) / dt, "ms_per_step": dt * 1e3, "tflops": flops / dt / 1e12,
+                     "energies": e.cpu().tolist()}
+        del ms
+    same = res["batched"]["energies"] == res["one_at_a_time"]["energies"]
+    for r in res.values():
+        r.pop("energies")
+    print(json.dumps({"case": "batch", "prec": args.prec, "n_meras": len(specs),
+                      "chis": [c for _, c, _ in specs], "steps": args.steps, "warmup": args.warmup,
+                      "results": res, "speedup": res["batched"]["mera_sweeps_per_s"] /
+                      res["one_at_a_time"]["mera_sweeps_per_s"], "identical_energies": same}), flush=True)
+
+
 def main():
     args = _args()
+    if args.case == "batch":
+        run_batch(args)
+        return
     if args.case != "sweep":
         run_case(args)
         return

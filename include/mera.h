@@ -215,6 +215,22 @@ typedef struct {
 mera_status mera_sweep(mera_state* state, const double* h1_dev, double shift, int n_pow, int prec,
                        void* ws, size_t ws_bytes, double* e_dev, void* stream);
 
+/*
+ * Many independent MERAs, one sweep each (each its own Hamiltonian, bond
+ * dimensions and precision-independent state): states[i] with h1[i]
+ * (device, [chi_b[0]^6]) and shift[i], scratch ws[i] of ws_bytes[i]
+ * (mera_sweep_workspace_size of that state), energy written to e_dev[i]
+ * (device), work issued on streams[i].  The sweeps run concurrently: a pool
+ * of n_threads host threads issues them, so that one MERA's host-side
+ * convergence checks do not hold back the others.  Each MERA's result is
+ * exactly what mera_sweep gives for it alone.  Returns the most severe
+ * status of the batch (MERA_ENOTCONV if only polar caps were hit); the
+ * error text names the MERA.  Streams and scratch must be distinct per MERA.
+ */
+mera_status mera_sweep_batch(mera_state* states, int n, const double* const* h1, const double* shift,
+                             int n_pow, int prec, void* const* ws, const size_t* ws_bytes, double* e_dev,
+                             void* const* streams, int n_threads);
+
 /* Scratch bytes for mera_sweep on a state with these dimensions. */
 mera_status mera_sweep_workspace_size(int n_layers, const int* chi_b, const int* chi_t, int prec,
                                       size_t* bytes);

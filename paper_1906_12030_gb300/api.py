@@ -20,7 +20,7 @@ __all__ = [
     "mera_energy", "mera_ising_h1", "mera_sweep", "mera_sweep_workspace_size", "mera_plan_json", "mera_flops",
     "workspace", "MeraState", "mera_launch_count", "mera_profile_enable", "mera_profile_read",
     "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE", "mera_device_status", "mera_gemm_test",
-    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose",
+    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_sweep_batch",
 ]
 
 PREC_F64, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3, 4
@@ -98,6 +98,8 @@ def library():
             "mera_gemm_test": ([i, vp, vp, i, i, i, vp, vp, sz, vp], i),
             "mera_ascend_noalloc": ([vp, vp, vp, i, i, vp, i, vp], i),
             "mera_op_transpose": ([vp, i, vp, vp], i),
+            "mera_sweep_batch": ([ctypes.POINTER(_State), i, ctypes.POINTER(vp), ctypes.POINTER(d), i, i,
+                                  ctypes.POINTER(vp), ctypes.POINTER(sz), vp, ctypes.POINTER(vp), i], i),
             "mera_profile_enable": ([i], i),
             "mera_profile_read": ([i, ctypes.POINTER(ctypes.c_longlong), pd, pd], i),
         }
@@ -362,3 +364,33 @@ def mera_op_transpose(x, d, out, stream=None):
     """out[I, J] = x[J, I] for a 3-site operator of local dimension d."""
     _check(library().mera_op_transpose(_f64(x, d ** 6, "x"), d, _f64(out, d ** 6, "out"), _stream(stream)))
     return out
+
+
+def mera_sweep_batch(states, h1s, shifts, n_pow, e_out, prec=PREC_F64, wss=None, streams=None, n_threads=8):
+    """One sweep of each of several independent MERAs, run concurrently.
+
+    states: list of MeraState; h1s: device h1 per MERA; shifts: floats;
+    e_out: device float64 tensor with one slot per MERA; wss: scratch per
+    MERA (allocated when None); streams: one torch.cuda.Stream per MERA."""
+    import torch
+
+    n = len(states)
+    if wss is None:
+        wss = [workspace(mera_sweep_workspace_size(s.chi_b, s.chi_t, prec), e_out.device) for s in states]
+    if streams is None:
+        streams = [torch.cuda.Stream(device=e_out.device) for _ in range(n)]
+    arr = (_State * n)(*[s._c() for s in states])
+    h_arr = (ctypes.c_void_p * n)(*[_f64(h, s.chi_b[0] ** 6, "h1").value for h, s in zip(h1s, states)])
+    sh_arr = (ctypes.c_double * n)(*[float(x) for x in shifts])
+    ws_arr = (ctypes.c_void_p * n)(*[w.data_ptr() for w in wss])
+    wb_arr = (ctypes.c_size_t * n)(*[w.numel() * w.element_size() for w in wss])
+    st_arr = (ctypes.c_void_p * n)(*[int(s.cuda_stream) for s in streams])
+    # the batch's streams must see the caller's pending work on the inputs
+    cur = torch.cuda.current_stream(e_out.device)
+    for s in streams:
+        s.wait_stream(cur)
+    _check(library().mera_sweep_batch(arr, n, h_arr, sh_arr, n_pow, prec, ws_arr, wb_arr,
+                                      _f64(e_out, n, "e_out"), st_arr, n_threads))
+    for s in streams:
+        cur.wait_stream(s)
+    return e_out

@@ -9,6 +9,7 @@
 #include <string>
 #include <atomic>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "../../include/mera.h"
@@ -683,4 +684,37 @@ extern "C" mera_status mera_op_transpose(const double* x, int d, double* out, vo
   st.row_src.n = 1; st.row_src.dim[0] = n; st.row_src.stride[0] = 1;
   st.col_src.n = 1; st.col_src.dim[0] = n; st.col_src.stride[0] = n;
   return cuda_status(launch_permute(st, x, out, 0, PREC_F64, static_cast<cudaStream_t>(stream)), "transpose");
+}
+
+extern "C" mera_status mera_sweep_batch(mera_state* states, int n, const double* const* h1, const double* shift,
+                                        int n_pow, int prec, void* const* ws, const size_t* ws_bytes, double* e_dev,
+                                        void* const* streams, int n_threads) {
+  if (!states || n < 1 || !h1 || !shift || !ws || !ws_bytes || !e_dev || !streams)
+    return fail(MERA_EINVAL, "null argument to mera_sweep_batch");
+  if (n_threads < 1) n_threads = 1;
+  n_threads = std::min(n_threads, n);
+  std::vector<mera_status> st(static_cast<size_t>(n), MERA_OK);
+  std::vector<std::string> msg(static_cast<size_t>(n));
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto worker = [&](int t) {
+    cudaSetDevice(dev);  // host threads start on device 0
+    for (int i = t; i < n; i += n_threads) {
+      st[size_t(i)] = mera_sweep(&states[i], h1[i], shift[i], n_pow, prec, ws[i], ws_bytes[i], e_dev + i, streams[i]);
+      if (st[size_t(i)] != MERA_OK) msg[size_t(i)] = g_err;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < n_threads; ++t) pool.emplace_back(worker, t);
+  worker(0);
+  for (auto& th : pool) th.join();
+  mera_status worst = MERA_OK;
+  for (int i = 0; i < n; ++i) {
+    if (st[size_t(i)] == MERA_OK) continue;
+    if (worst == MERA_OK || (worst == MERA_ENOTCONV && st[size_t(i)] != MERA_ENOTCONV)) {
+      worst = st[size_t(i)];
+      g_err = "MERA " + std::to_string(i) + ": " + msg[size_t(i)];
+    }
+  }
+  return worst;
 }

@@ -77,6 +77,12 @@ def _peak_tflops(prec: str):
     return base * NOMINAL[prec] / NOMINAL["bf16"], src
 
 
+# DRAM bytes per launch of the chi^9-class GEMMs, from the ncu capture named
+# here (profiles/).  Reported only for the workload it was taken on; it must
+# be retaken (or set to None) whenever the kernel changes.
+ROOFLINE_TRAFFIC = {("bf16x3", 16): (1.119e9, "profiles/tc_gemm_8warp_bf16x3_chi16_ascend.md")}
+
+
 def _sweep_flops(m, chi):
     import mera_inputs as I
 
@@ -360,7 +366,9 @@ def run_native(args):
         "energy_per_spin": energy,
         "fp64": fp64,
         "roofline": {"bound": "tensor" if args.prec != "f64" else "fp64", "achieved": dom_tflops, "peak": peak,
-                     "unit": "TFLOP/s", "frac": (dom_tflops / peak) if dom_tflops else None, "traffic": None,
+                     "unit": "TFLOP/s", "frac": (dom_tflops / peak) if dom_tflops else None,
+                     "traffic": ROOFLINE_TRAFFIC.get((args.prec, chi), (None, None))[0],
+                     "traffic_source": ROOFLINE_TRAFFIC.get((args.prec, chi), (None, None))[1],
                      "kernel": "gemm_f64_kernel" if args.prec == "f64" else "tcgen05 GEMM",
                      "launches": dom[0], "kernel_ms": dom[1], "peak_source": f"{peak_src} bf16 x nominal ratio"},
         "stage_ms_per_step": {"gemm": allg[1] / args.steps, "gemm_dominant": dom[1] / args.steps,

@@ -395,9 +395,31 @@ def run_case(args):
     chi, prec = args.chi, m.PRECS[args.prec]
     rng = np.random.default_rng(SEED)
     u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
-    h, rho = I.random_operator(rng, chi), I.random_density(rng, chi)
     d = lambda x: torch.from_numpy(x).cuda().reshape(-1)  # noqa: E731
-    hd, rd, ud, wd = d(h), d(rho), d(u), d(w)
+    ud, wd = d(u), d(w)
+    need_h = args.case != "descend"
+    need_rho = args.case != "ascend"
+    if chi < 24:
+        hd = d(I.random_operator(rng, chi)) if need_h else None
+        rd = d(I.random_density(rng, chi)) if need_rho else None
+    else:
+        # chi^3 x chi^3 operators (33 GB each at chi = 40): seeded symmetric
+        # Gaussians drawn on the device, rho scaled to unit trace.  The maps
+        # are linear, so the timing does not depend on positivity.
+        g = torch.Generator(device="cuda")
+        g.manual_seed(SEED)
+
+        def sym(trace_one):
+            n3 = chi ** 3
+            x = torch.randn(n3, n3, dtype=torch.float64, device="cuda", generator=g)
+            x.add_(x.t().contiguous()).mul_(0.5)
+            if trace_one:
+                x.diagonal().add_(1.0 / n3 - float(x.diagonal().sum()) / n3)
+            return x.reshape(-1)
+
+        hd = sym(False) if need_h else None
+        rd = sym(True) if need_rho else None
+        torch.cuda.empty_cache()
     op = {"ascend": m.OP_ASCEND, "descend": m.OP_DESCEND, "env_u": m.OP_ENV_U, "env_w": m.OP_ENV_W}[args.case]
     ws = m.workspace(m.mera_workspace_size(op, chi, chi, prec))
     out = torch.empty(chi ** 6, dtype=torch.float64, device="cuda")

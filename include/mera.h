@@ -322,6 +322,18 @@ mera_status mera_ascend_noalloc(const double* h, const double* u, const double* 
                                 double* h_out, int prec, void* stream);
 
 /*
+ * Memory knob (no counterpart in the paper): a rank-7 intermediate of the
+ * chi^9 contraction pairs larger than `bytes` (default 16 GiB) is computed
+ * one slice at a time -- the pair runs once per value of one of its free
+ * legs on a buffer a factor chi smaller -- so that chi = 40 fits in HBM.
+ * Results agree with the unsliced program up to rounding (a smaller slice
+ * GEMM may split its K range where the whole one did not).  Changing it
+ * discards the cached contraction programs;
+ * call it when no call of this library is in flight.
+ */
+mera_status mera_set_slice_bytes(size_t bytes);
+
+/*
  * Test hook (no counterpart in the paper): C = A * B^T through the GEMM
  * kernel of mode prec, with A row-major M x K, B row-major N x K and C
  * row-major M x N, all binary64 device arrays.  The operands are first cast

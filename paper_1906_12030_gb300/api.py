@@ -20,7 +20,7 @@ __all__ = [
     "mera_energy", "mera_ising_h1", "mera_sweep", "mera_sweep_workspace_size", "mera_plan_json", "mera_flops",
     "workspace", "MeraState", "mera_launch_count", "mera_profile_enable", "mera_profile_read",
     "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE", "mera_device_status", "mera_gemm_test",
-    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_sweep_batch",
+    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_sweep_batch", "mera_set_slice_bytes",
 ]
 
 PREC_F64, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3, 4
@@ -98,6 +98,7 @@ def library():
             "mera_gemm_test": ([i, vp, vp, i, i, i, vp, vp, sz, vp], i),
             "mera_ascend_noalloc": ([vp, vp, vp, i, i, vp, i, vp], i),
             "mera_op_transpose": ([vp, i, vp, vp], i),
+            "mera_set_slice_bytes": ([sz], i),
             "mera_sweep_batch": ([ctypes.POINTER(_State), i, ctypes.POINTER(vp), ctypes.POINTER(d), i, i,
                                   ctypes.POINTER(vp), ctypes.POINTER(sz), vp, ctypes.POINTER(vp), i], i),
             "mera_profile_enable": ([i], i),
@@ -394,3 +395,8 @@ def mera_sweep_batch(states, h1s, shifts, n_pow, e_out, prec=PREC_F64, wss=None,
     for s in streams:
         cur.wait_stream(s)
     return e_out
+
+
+def mera_set_slice_bytes(nbytes: int) -> None:
+    """Slice rank-7 intermediates larger than nbytes (default 16 GiB)."""
+    _check(library().mera_set_slice_bytes(int(nbytes)))

@@ -150,16 +150,16 @@ mera_status run_program(const OpProgram& prog, const double* const inputs[4], do
       ProfScope ps(stream, 0, g.dominant, g.flops);
       if (prec == PREC_F64) {
         GemmF64Args args;
-        args.A = reinterpret_cast<const double*>(ws + a.offset);
+        args.A = reinterpret_cast<const double*>(ws + a.offset) + g.a_off;
         args.a_m = g.lda;
         args.a_k = 1;
-        args.B = reinterpret_cast<const double*>(ws + b.offset);
+        args.B = reinterpret_cast<const double*>(ws + b.offset) + g.b_off;
         args.b_n = g.ldb;
         args.b_k = 1;
         args.M = g.M;
         args.N = g.N;
         args.K = g.K;
-        args.C = g.c_buf >= 0 ? reinterpret_cast<double*>(ws + dg.bufs[g.c_buf].offset) : out;
+        args.C = (g.c_buf >= 0 ? reinterpret_cast<double*>(ws + dg.bufs[g.c_buf].offset) : out) + g.c_off;
         args.m_dst = g.m_dst;
         args.n_dst = g.n_dst;
         args.alpha = g.alpha;
@@ -169,17 +169,19 @@ mera_status run_program(const OpProgram& prog, const double* const inputs[4], do
       } else {
         TcGemmArgs args;
         args.prec = prec;
-        args.A = ws + a.offset;
+        const int64_t eb = elem_bytes(prec);
+        args.A = ws + a.offset + g.a_off * eb;
         args.a_plane_bytes = a.plane_bytes;
         args.lda = g.lda;
-        args.B = ws + b.offset;
+        args.B = ws + b.offset + g.b_off * eb;
         args.b_plane_bytes = b.plane_bytes;
         args.ldb = g.ldb;
         args.M = g.M;
         args.N = g.N;
         args.K = g.K;
         args.c_final = g.c_buf < 0;
-        args.C = g.c_buf >= 0 ? static_cast<void*>(ws + dg.bufs[g.c_buf].offset) : static_cast<void*>(out);
+        args.C = g.c_buf >= 0 ? static_cast<void*>(ws + dg.bufs[g.c_buf].offset + g.c_off * eb)
+                              : static_cast<void*>(out + g.c_off);
         args.c_plane_elems = g.c_buf >= 0 ? dg.bufs[g.c_buf].plane_bytes / elem_bytes(prec) : 0;
         args.m_dst = g.m_dst;
         args.n_dst = g.n_dst;
@@ -717,4 +719,9 @@ extern "C" mera_status mera_sweep_batch(mera_state* states, int n, const double*
     }
   }
   return worst;
+}
+
+extern "C" mera_status mera_set_slice_bytes(size_t bytes) {
+  set_slice_bytes(bytes);
+  return MERA_OK;
 }

@@ -234,9 +234,14 @@ struct Builder {
     std::vector<int> mlegs, nlegs, klegs;
   };
   std::vector<G> g;
+  // Slicing of rank-7 intermediates: slice_leg[P2] = leg, sliced_child[P2] =
+  // P1 (the producer, emitted inside P2's slice loop).
+  std::vector<int> slice_leg, sliced_child;
+  std::vector<char> deferred;
+  size_t slice_threshold = 0;
 
-  Builder(const Diagram& d, const int64_t* dm, int p, double al, int acc)
-      : dg(d), dim(dm), prec(p), alpha(al), accumulate(acc) {}
+  Builder(const Diagram& d, const int64_t* dm, int p, double al, int acc, size_t sb)
+      : dg(d), dim(dm), prec(p), alpha(al), accumulate(acc), slice_threshold(sb) {}
 
   int64_t prod(const std::vector<int>& legs) const {
     int64_t s = 1;
@@ -276,6 +281,89 @@ struct Builder {
     return round_up(std::max<int64_t>(cols, 1), align);
   }
 
+  // One GEMM step for node i; with slice leg l >= 0 the step covers l = v
+  // only: the operand holding l is read from row block v (l is its
+  // outermost row leg), the sliced intermediate lives in a one-slice buffer,
+  // and the consumer writes its output at offset v * stride(l).
+  void emit_gemm(int i, int l, int64_t v, std::vector<int>& first_use, std::vector<int>& last_use) {
+    const G& gi = g[i];
+    Step s;
+    s.kind = 1;
+    GemmStep& gs = s.g;
+    gs.a_buf = buf_of[gi.a];
+    gs.b_buf = buf_of[gi.b];
+    std::vector<int> ml = gi.mlegs, nl = gi.nlegs;
+    const bool full_flops_dominant_hint = (l >= 0);
+    gs.M = prod(ml);
+    gs.N = prod(nl);
+    gs.K = prod(gi.klegs);
+    gs.lda = prog.bufs[gs.a_buf].ld;
+    gs.ldb = prog.bufs[gs.b_buf].ld;
+    gs.c_buf = (i == tr.root) ? -1 : buf_of[i];
+    gs.c_ld = (i == tr.root) ? 0 : prog.bufs[buf_of[i]].ld;
+    const bool is_producer = (l >= 0) && deferred[i];  // writes the one-slice buffer
+    if (l >= 0) {
+      const bool in_m = !ml.empty() && ml.front() == l;
+      const bool in_n = !nl.empty() && nl.front() == l;
+      const int64_t dl = dim[l];
+      // The producer reads row block v of its operand on l's side; the
+      // consumer's operand on that side is the one-slice buffer itself.
+      if (in_m) {
+        ml.erase(ml.begin());
+        gs.M /= dl;
+        gs.a_off = is_producer ? v * gs.M * gs.lda : 0;
+      } else if (in_n) {
+        nl.erase(nl.begin());
+        gs.N /= dl;
+        gs.b_off = is_producer ? v * gs.N * gs.ldb : 0;
+      }
+      gs.c_off = is_producer ? 0 : v * dst_stride[i].at(l);
+    }
+    gs.m_dst = legmap(ml, dst_stride[i]);
+    gs.n_dst = legmap(nl, dst_stride[i]);
+    gs.alpha = (i == tr.root) ? alpha : 1.0;
+    gs.accumulate = (i == tr.root) ? accumulate : 0;
+    gs.flops = 2.0 * double(gs.M) * double(gs.N) * double(gs.K);
+    gs.dominant = full_flops_dominant_hint ? 2 : 0;  // resolved after emission
+    gs.split = tc_split_k(prec, gs.M, gs.N, gs.K);
+    if (gs.split > 1) {  // FP32 partials [split][N][M], live during this step only
+      Buffer pb;
+      pb.rows = int64_t(gs.split) * gs.N;
+      pb.ld = gs.M;
+      pb.plane_bytes = round_up(pb.rows * pb.ld * 4, 256);
+      pb.bytes = pb.plane_bytes;
+      prog.bufs.push_back(pb);
+      gs.p_buf = int(prog.bufs.size()) - 1;
+      first_use.push_back(-1);
+      last_use.push_back(-1);
+    }
+    {
+      std::vector<int> kl = gi.klegs;
+      auto a_legs = gi.mlegs;
+      a_legs.insert(a_legs.end(), kl.begin(), kl.end());
+      auto b_legs = gi.nlegs;
+      b_legs.insert(b_legs.end(), kl.begin(), kl.end());
+      std::vector<std::pair<int64_t, int>> o;
+      for (int x : gi.mlegs) o.push_back({dst_stride[i].at(x), x});
+      for (int x : gi.nlegs) o.push_back({dst_stride[i].at(x), x});
+      std::sort(o.begin(), o.end(), [](auto& x, auto& y) { return x.first > y.first; });
+      std::vector<int> ol;
+      for (auto& pr : o) ol.push_back(pr.second);
+      gs.label = legs_str(a_legs) + "*" + legs_str(b_legs) + "->" + legs_str(ol);
+      if (l >= 0) gs.label += std::string("[") + label_char(l) + "=" + std::to_string(v) + "]";
+    }
+    prog.flops += gs.flops;
+    prog.steps.push_back(s);
+    const int si = int(prog.steps.size()) - 1;
+    if (last_use[gs.a_buf] < si) last_use[gs.a_buf] = si;
+    if (last_use[gs.b_buf] < si) last_use[gs.b_buf] = si;
+    if (gs.p_buf >= 0) first_use[gs.p_buf] = last_use[gs.p_buf] = si;
+    if (gs.c_buf >= 0) {
+      if (first_use[gs.c_buf] < 0) first_use[gs.c_buf] = si;
+      if (last_use[gs.c_buf] < si) last_use[gs.c_buf] = si;
+    }
+  }
+
   bool build() {
     const int n = int(dg.tensors.size());
     std::vector<uint64_t> tmask(n, 0);
@@ -299,6 +387,40 @@ struct Builder {
       gi.b = (fl >= fr) ? nd.right : nd.left;
       gi.klegs = legs_list(K);
     }
+    // Slicing pre-pass: a rank-7 intermediate T (the product of the two
+    // chi^9 GEMMs) bigger than the threshold is cut over one of its legs
+    // that stays free in the consumer, the largest one.
+    slice_leg.assign(nn, -1);
+    sliced_child.assign(nn, -1);
+    deferred.assign(nn, 0);
+    for (size_t i = 0; i < nn; ++i) {
+      const Node& nd = tr.nodes[i];
+      if (nd.tensor >= 0) continue;
+      for (int c : {g[i].a, g[i].b}) {
+        const Node& cn = tr.nodes[c];
+        if (cn.tensor >= 0 || popcount64(cn.legs) != 7) continue;
+        const double bytes = size_of(cn.legs, dim) * elem_bytes(prec) * planes(prec);
+        if (bytes <= double(slice_threshold)) continue;
+        const uint64_t K2 = tr.nodes[g[i].a].legs & tr.nodes[g[i].b].legs;
+        int best = -1;
+        for (int l : legs_list(cn.legs & ~K2))
+          if (best < 0 || dim[l] > dim[best]) best = l;
+        if (best < 0 || dim[best] < 2) continue;
+        slice_leg[i] = best;
+        sliced_child[i] = c;
+        deferred[c] = 1;
+        break;
+      }
+    }
+    // A sliced intermediate is produced inside its consumer's loop by one
+    // GEMM per slice, so it cannot itself run a slice loop of its own: keep
+    // its child whole in that case.
+    for (size_t i = 0; i < nn; ++i)
+      if (deferred[i] && slice_leg[i] >= 0) {
+        deferred[sliced_child[i]] = 0;
+        sliced_child[i] = -1;
+        slice_leg[i] = -1;
+      }
     // Root output layout: the caller's order of the open legs.
     {
       std::vector<int> out;
@@ -350,6 +472,14 @@ struct Builder {
         klegs.erase(std::find(klegs.begin(), klegs.end(), prefer));
         klegs.push_back(prefer);
       }
+      if (slice_leg[i] >= 0) {  // the sliced leg outermost on T's side
+        std::vector<int>& side = (sliced_child[i] == gi.a) ? mlegs : nlegs;
+        auto it = std::find(side.begin(), side.end(), slice_leg[i]);
+        if (it != side.end()) {
+          side.erase(it);
+          side.insert(side.begin(), slice_leg[i]);
+        }
+      }
       gi.mlegs = mlegs;
       gi.nlegs = nlegs;
       gi.klegs = klegs;
@@ -361,6 +491,7 @@ struct Builder {
       for (int c : {gi.a, gi.b}) {
         Buffer b;
         b.rows = (c == gi.a) ? prod(mlegs) : prod(nlegs);
+        if (c == sliced_child[i]) b.rows /= dim[slice_leg[i]];  // one slice at a time
         b.ld = ld;
         b.plane_bytes = round_up(b.rows * ld * elem_bytes(prec), 256);
         b.bytes = b.plane_bytes * planes(prec);
@@ -412,63 +543,22 @@ struct Builder {
         if (ts.slot == SLOT_U || ts.slot == SLOT_W) prog.bufs[p.dst_buf].resident = 1;
         continue;
       }
-      const G& gi = g[i];
-      Step s;
-      s.kind = 1;
-      GemmStep& gs = s.g;
-      gs.a_buf = buf_of[gi.a];
-      gs.b_buf = buf_of[gi.b];
-      gs.M = prod(gi.mlegs);
-      gs.N = prod(gi.nlegs);
-      gs.K = prod(gi.klegs);
-      gs.lda = prog.bufs[gs.a_buf].ld;
-      gs.ldb = prog.bufs[gs.b_buf].ld;
-      gs.c_buf = (i == tr.root) ? -1 : buf_of[i];
-      gs.c_ld = (i == tr.root) ? 0 : prog.bufs[buf_of[i]].ld;
-      gs.m_dst = legmap(gi.mlegs, dst_stride[i]);
-      gs.n_dst = legmap(gi.nlegs, dst_stride[i]);
-      gs.alpha = (i == tr.root) ? alpha : 1.0;
-      gs.accumulate = (i == tr.root) ? accumulate : 0;
-      gs.flops = 2.0 * double(gs.M) * double(gs.N) * double(gs.K);
-      gs.split = tc_split_k(prec, gs.M, gs.N, gs.K);
-      if (gs.split > 1) {  // FP32 partials [split][N][M], live during this step only
-        Buffer pb;
-        pb.rows = int64_t(gs.split) * gs.N;
-        pb.ld = gs.M;
-        pb.plane_bytes = round_up(pb.rows * pb.ld * 4, 256);
-        pb.bytes = pb.plane_bytes;
-        prog.bufs.push_back(pb);
-        gs.p_buf = int(prog.bufs.size()) - 1;
-        first_use.push_back(-1);
-        last_use.push_back(-1);
+      if (deferred[i]) continue;  // emitted inside its consumer's slice loop
+      if (slice_leg[i] < 0) {
+        emit_gemm(i, -1, 0, first_use, last_use);
+        continue;
       }
-      {
-        std::vector<int> kl = gi.klegs;
-        auto a_legs = gi.mlegs;
-        a_legs.insert(a_legs.end(), kl.begin(), kl.end());
-        auto b_legs = gi.nlegs;
-        b_legs.insert(b_legs.end(), kl.begin(), kl.end());
-        std::vector<std::pair<int64_t, int>> o;
-        for (int l : gi.mlegs) o.push_back({dst_stride[i].at(l), l});
-        for (int l : gi.nlegs) o.push_back({dst_stride[i].at(l), l});
-        std::sort(o.begin(), o.end(), [](auto& x, auto& y) { return x.first > y.first; });
-        std::vector<int> ol;
-        for (auto& pr : o) ol.push_back(pr.second);
-        gs.label = legs_str(a_legs) + "*" + legs_str(b_legs) + "->" + legs_str(ol);
+      const int l = slice_leg[i];
+      for (int64_t v = 0; v < dim[l]; ++v) {
+        emit_gemm(sliced_child[i], l, v, first_use, last_use);
+        emit_gemm(i, l, v, first_use, last_use);
       }
-      prog.flops += gs.flops;
-      prog.steps.push_back(s);
-      const int si = int(prog.steps.size()) - 1;
-      last_use[gs.a_buf] = si;
-      last_use[gs.b_buf] = si;
-      if (gs.p_buf >= 0) first_use[gs.p_buf] = last_use[gs.p_buf] = si;
-      if (gs.c_buf >= 0) first_use[gs.c_buf] = si;
     }
     double fmax = 0.0;
     for (const Step& st : prog.steps)
-      if (st.kind == 1) fmax = std::max(fmax, st.g.flops);
+      if (st.kind == 1 && st.g.dominant != 2) fmax = std::max(fmax, st.g.flops);
     for (Step& st : prog.steps)
-      if (st.kind == 1) st.g.dominant = st.g.flops >= 0.25 * fmax;
+      if (st.kind == 1) st.g.dominant = (st.g.dominant == 2) || st.g.flops >= 0.25 * fmax;
     // Resident buffers (operand copies of u and w) are packed one after the
     // other and never reused, so a caller may run the program again with the
     // same u and w without repeating those copies.  Offsets here are
@@ -515,6 +605,7 @@ struct Key {
 
 std::mutex g_mu;
 std::map<Key, std::unique_ptr<OpProgram>> g_cache;
+size_t g_slice_bytes = size_t(16) << 30;  // 16 GiB
 
 }  // namespace
 
@@ -533,7 +624,7 @@ const OpProgram* get_program(int op, int chi_b, int chi_t, int prec) {
   auto prog = std::make_unique<OpProgram>();
   const std::vector<Diagram> ds = diagrams_of(op);
   for (size_t d = 0; d < ds.size(); ++d) {
-    Builder b(ds[d], dim, prec, 0.5, d == 0 ? 0 : 1);
+    Builder b(ds[d], dim, prec, 0.5, d == 0 ? 0 : 1, g_slice_bytes);
     if (!b.build()) return nullptr;
     prog->flops += b.prog.flops;
     prog->diagrams.push_back(std::move(b.prog));
@@ -555,6 +646,17 @@ const OpProgram* get_program(int op, int chi_b, int chi_t, int prec) {
   const OpProgram* out = prog.get();
   g_cache[k] = std::move(prog);
   return out;
+}
+
+void set_slice_bytes(size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_slice_bytes = bytes;
+  g_cache.clear();
+}
+
+size_t slice_bytes() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_slice_bytes;
 }
 
 std::string program_json(const OpProgram& prog, int op, int chi_b, int chi_t, int prec) {
@@ -594,7 +696,8 @@ std::string program_json(const OpProgram& prog, int op, int chi_b, int chi_t, in
           << ",\"M\":" << g.M << ",\"N\":" << g.N << ",\"K\":" << g.K << ",\"lda\":" << g.lda << ",\"ldb\":" << g.ldb
           << ",\"c_buf\":" << g.c_buf << ",\"alpha\":" << g.alpha << ",\"accumulate\":" << g.accumulate
           << ",\"flops\":" << g.flops << ",\"dominant\":" << g.dominant << ",\"split\":" << g.split
-          << ",\"p_buf\":" << g.p_buf << ",\"m_dst\":";
+          << ",\"p_buf\":" << g.p_buf << ",\"a_off\":" << g.a_off << ",\"b_off\":" << g.b_off
+          << ",\"c_off\":" << g.c_off << ",\"m_dst\":";
         lm(g.m_dst);
         o << ",\"n_dst\":";
         lm(g.n_dst);

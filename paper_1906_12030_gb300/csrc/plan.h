@@ -53,6 +53,7 @@ struct GemmStep {
   double flops = 0.0;
   int dominant = 0;   // one of the chi^9-class steps of its diagram
   int split = 1;      // K split over this many CTAs (tensor-core modes; partials summed in FP64)
+  int64_t a_off = 0, b_off = 0, c_off = 0;  // element offsets into A, B and the destination (slices)
   int p_buf = -1;     // FP32 partial-sum buffer [split][N][M] when split > 1
   std::string label;  // e.g. "aceiq*CDcdil->ADadelq" for inspection
 };
@@ -101,5 +102,11 @@ int planes(int prec);       // 2 for BF16X3 (hi, lo), 3 for BF16X6 (hi, mid, lo)
 const OpProgram* get_program(int op, int chi_b, int chi_t, int prec);
 
 std::string program_json(const OpProgram& prog, int op, int chi_b, int chi_t, int prec);
+
+// Rank-7 intermediates larger than this many bytes are sliced over one leg
+// (the pair of chi^9 GEMMs around them runs once per value of that leg, on
+// a one-slice buffer).  Setting it clears the program cache.
+void set_slice_bytes(size_t bytes);
+size_t slice_bytes();
 
 }  // namespace mera

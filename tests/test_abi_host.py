@@ -128,14 +128,17 @@ def _emulate(plan, inputs, out_size):
                 a, bb = bufs[st["a_buf"]], bufs[st["b_buf"]]
                 M, N, K = st["M"], st["N"], st["K"]
                 # operand reads (TMA boxes are clipped to rows x K of these planes)
-                assert M <= a["rows"] and N <= bb["rows"] and K <= st["lda"] == a["ld"] and K <= st["ldb"] == bb["ld"]
-                A = arena[a["offset"] // eb + np.arange(M)[:, None] * st["lda"] + np.arange(K)[None, :]]
-                B = arena[bb["offset"] // eb + np.arange(N)[:, None] * st["ldb"] + np.arange(K)[None, :]]
+                assert K <= st["lda"] == a["ld"] and K <= st["ldb"] == bb["ld"]
+                # a slice step reads a row block of its operand: whole rows only
+                assert st["a_off"] % st["lda"] == 0 and st["b_off"] % st["ldb"] == 0
+                assert st["a_off"] // st["lda"] + M <= a["rows"] and st["b_off"] // st["ldb"] + N <= bb["rows"]
+                A = arena[a["offset"] // eb + st["a_off"] + np.arange(M)[:, None] * st["lda"] + np.arange(K)[None, :]]
+                B = arena[bb["offset"] // eb + st["b_off"] + np.arange(N)[:, None] * st["ldb"] + np.arange(K)[None, :]]
                 assert not np.isnan(A).any() and not np.isnan(B).any()
                 C = st["alpha"] * (A @ B.T)
                 mo = _offsets(st["m_dst"], M)
                 no = _offsets(st["n_dst"], N)
-                idx = mo[:, None] + no[None, :]
+                idx = st["c_off"] + mo[:, None] + no[None, :]
                 assert len(np.unique(idx)) == idx.size  # the scatter is a bijection
                 if st["c_buf"] < 0:
                     assert idx.min() >= 0 and idx.max() < out_size
@@ -174,6 +177,52 @@ def test_programs_reproduce_oracle(prec, chi_b, chi_t):
         plan = m.mera_plan_json(op, chi_b, chi_t, prec)
         got = _emulate(plan, inputs, want.size).reshape(want.shape)
         assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max()), op
+
+
+@pytest.fixture
+def forced_slicing():
+    """Slice every rank-7 intermediate, whatever its size."""
+    m.mera_set_slice_bytes(0)
+    try:
+        yield
+    finally:
+        m.mera_set_slice_bytes(16 << 30)
+
+
+@pytest.mark.parametrize("prec,chi_b,chi_t", [(m.PREC_F64, 3, 3), (m.PREC_BF16X3, 2, 3), (m.PREC_F64, 4, 3),
+                                              (m.PREC_BF16X6, 3, 5)])
+def test_sliced_programs_reproduce_oracle(forced_slicing, prec, chi_b, chi_t):
+    """Rank-7 intermediates computed one slice at a time (the memory plan
+    that lets chi = 40 fit) still give the oracle's maps, and every diagram
+    holding a chi^9 pair does slice it."""
+    rng = np.random.default_rng(11)
+    u, w = I.random_u(rng, chi_b), I.random_w(rng, chi_b, chi_t)
+    h = I.random_operator(rng, chi_b, symmetric=False)
+    rho = I.random_operator(rng, chi_t, symmetric=False)
+    hs, rs = I.random_operator(rng, chi_b), I.random_density(rng, chi_t)
+    cases = {m.OP_ASCEND: ([h, None, u, w], O.ascend(h, u, w)),
+             m.OP_DESCEND: ([None, rho, u, w], O.descend(rho, u, w)),
+             m.OP_ENV_U: ([hs, rs, u, w], O.env_u(hs, rs, u, w)),
+             m.OP_ENV_W: ([hs, rs, u, w], O.env_w(hs, rs, u, w))}
+    for op, (inputs, want) in cases.items():
+        plan = m.mera_plan_json(op, chi_b, chi_t, prec)
+        sliced = [st for dg in plan["diagrams"] for st in dg["steps"] if st["kind"] == "gemm" and "=" in st["label"]]
+        assert sliced, op
+        got = _emulate(plan, inputs, want.size).reshape(want.shape)
+        assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max()), op
+
+
+def test_slicing_shrinks_the_chi40_workspace():
+    """At chi = 40 the unsliced rank-7 intermediates alone take hundreds of
+    GB; with the default threshold the descend workspace fits in HBM."""
+    need = m.mera_workspace_size(m.OP_DESCEND, 40, 40, m.PREC_BF16X3)
+    assert need < 200 * 2**30
+    m.mera_set_slice_bytes(1 << 62)
+    try:
+        whole = m.mera_workspace_size(m.OP_DESCEND, 40, 40, m.PREC_BF16X3)
+    finally:
+        m.mera_set_slice_bytes(16 << 30)
+    assert whole > 300 * 2**30
 
 
 def test_split_k_partials_do_not_overlap_live_buffers():

@@ -105,6 +105,30 @@ def test_maps_mixed_precision(prec, chi_b, chi_t):
         assert e < MAP_TOL[prec], (name, e)
 
 
+@pytest.mark.parametrize("prec", [m.PREC_F64, m.PREC_BF16X3, m.PREC_BF16])
+@pytest.mark.parametrize("chi_b,chi_t", [(4, 4), (8, 8), (4, 16)])
+def test_sliced_maps(prec, chi_b, chi_t):
+    """Rank-7 intermediates computed one slice at a time (forced here at
+    small chi; by default only above 16 GiB) give the oracle's maps within
+    the mode's tolerance, and agree with the unsliced program."""
+    whole = _maps(prec, chi_b, chi_t, 5)
+    m.mera_set_slice_bytes(0)
+    try:
+        plan = m.mera_plan_json(m.OP_ENV_W, chi_b, chi_t, prec)
+        assert any("=" in st["label"] for dg in plan["diagrams"] for st in dg["steps"] if st["kind"] == "gemm")
+        res = _maps(prec, chi_b, chi_t, 5)
+        torch.cuda.synchronize()
+    finally:
+        m.mera_set_slice_bytes(16 << 30)
+    tol = 1e-10 if prec == m.PREC_F64 else MAP_TOL[prec]
+    for name, (got, want) in res.items():
+        g = got.cpu().numpy().reshape(want.shape)
+        w0 = whole[name][0].cpu().numpy().reshape(want.shape)
+        scale = np.abs(want).max()
+        assert np.abs(g - want).max() / scale < tol, name
+        assert np.abs(g - w0).max() / scale < tol, name
+
+
 @pytest.mark.parametrize("prec", TC_PRECS)
 def test_fixed_point_and_energy_mixed(prec):
     chi = 4

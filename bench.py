@@ -49,9 +49,16 @@ def _args():
     ap.add_argument("--prec", default="bf16x3", choices=["f64", "tf32", "bf16", "bf16x3", "bf16x6"])
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed FP64 sweeps (after one untimed) for the mixed-vs-FP64 comparison; 0 skips it")
+    ap.add_argument("--slice-gib", type=float, default=None,
+                    help="slice rank-7 intermediates larger than this many GiB (library default 16)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--case", default="sweep", choices=["sweep", "ascend", "descend", "env_u", "env_w", "batch"],
+    ap.add_argument("--sweeps", type=int, default=300, help="--case precision: optimisation sweeps per run")
+    ap.add_argument("--polish", type=int, default=20, help="--case precision: FP64 sweeps after the mixed ones")
+    ap.add_argument("--scaling-k", type=int, default=0,
+                    help="--case precision: also compare this many scaling dimensions (mixed vs FP64)")
+    ap.add_argument("--case", default="sweep",
+                    choices=["sweep", "ascend", "descend", "env_u", "env_w", "batch", "precision"],
                     help="sweep: the benchmark; otherwise time one map call (after one warm call), for profiling")
     return ap.parse_args()
 
@@ -80,7 +87,7 @@ def _peak_tflops(prec: str):
 # DRAM bytes per launch of the chi^9-class GEMMs, from the ncu capture named
 # here (profiles/).  Reported only for the workload it was taken on; it must
 # be retaken (or set to None) whenever the kernel changes.
-ROOFLINE_TRAFFIC = {("bf16x3", 16): (1.119e9, "profiles/tc_gemm_8warp_bf16x3_chi16_ascend.md")}
+ROOFLINE_TRAFFIC = {}
 
 
 def _sweep_flops(m, chi):
@@ -518,10 +525,110 @@ def run_batch(args):
                       res["one_at_a_time"]["mera_sweeps_per_s"], "identical_energies": same}), flush=True)
 
 
+def run_precision(args):
+    """Mixed precision against FP64 on the same MERA (same seed, same sweep count):
+    - ref:    S sweeps with FP64 contractions;
+    - mixed:  S sweeps in the mixed mode;
+    - polish: S - P mixed sweeps, then P FP64 sweeps.
+    Each final state is evaluated in FP64 (rho* by 60 power steps from its warm
+    start, descent to the bottom layer, energy per spin); the mixed state is
+    also evaluated in the mixed mode.  All contractions run in the library."""
+    import numpy as np
+    import torch
+
+    import mera_inputs as I
+    import paper_1906_12030_gb300 as m
+    from paper_1906_12030_gb300 import scaling
+
+    dev = torch.device("cuda", 0)
+    chi, prec = args.chi, m.PRECS[args.prec]
+    h1_host, shift = m.mera_ising_h1(HZ)
+    h1 = torch.from_numpy(h1_host.reshape(-1)).to(dev)
+    S, P = args.sweeps, min(args.polish, args.sweeps)
+
+    def fresh():
+        layers = I.init_mera(SEED, chi)
+        us = [torch.from_numpy(u).to(dev).reshape(-1).contiguous() for u, _ in layers]
+        ws_ = [torch.from_numpy(w).to(dev).contiguous() for _, w in layers]
+        n3 = chi ** 3
+        rho = (torch.eye(n3, dtype=torch.float64, device=dev) / n3).reshape(-1).contiguous()
+        return m.MeraState(us, ws_, rho), us, ws_, rho
+
+    def run(state, schedule):
+        e = torch.empty(1, dtype=torch.float64, device=dev)
+        wss = {}
+        hist = []
+        t0 = time.perf_counter()
+        for p in schedule:
+            if p not in wss:
+                wss[p] = m.workspace(m.mera_sweep_workspace_size(state.chi_b, state.chi_t, p), dev)
+            try:
+                m.mera_sweep(state, h1, shift, N_POW, e, prec=p, ws=wss[p])
+            except m.MeraNotConverged:
+                pass
+            hist.append(e)
+            e = torch.empty(1, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        return [float(x.item()) for x in hist], time.perf_counter() - t0
+
+    def evaluate(us, ws_, rho_star, p):
+        """Energy per spin of a state, every map in mode p."""
+        dims = I.layer_dims(chi)
+        n = len(dims)
+        rho = rho_star.clone()
+        ws_fp = m.workspace(m.mera_workspace_size(m.OP_FIXED_POINT, chi, chi, p), dev)
+        m.mera_fixed_point_rho(us[-1], ws_[-1], chi, rho, 60, prec=p, ws=ws_fp)
+        for t in range(n - 2, 0, -1):  # rho* sits on top of layer n-2; descend to the top of layer 0
+            cb, ct = dims[t]
+            out = torch.empty(cb ** 6, dtype=torch.float64, device=dev)
+            m.mera_descend(rho, us[t], ws_[t], cb, ct, out, prec=p)
+            rho = out
+        cb, ct = dims[0]
+        e = torch.empty(1, dtype=torch.float64, device=dev)
+        m.mera_energy(h1, rho, us[0], ws_[0], cb, ct, e, prec=p)
+        return 0.5 * (float(e.item()) + shift)
+
+    out = {"case": "precision", "chi": chi, "prec": args.prec, "sweeps": S, "polish_fp64_sweeps": P,
+           "exact_infinite_chain": -4.0 / np.pi}
+    st, us, ws_, rho = fresh()
+    hist_m, t_m = run(st, [prec] * S)
+    out["mixed"] = {"sweep_energy_last": hist_m[-1], "sweep_energy_change_last10": hist_m[-1] - hist_m[-11]
+                    if S > 10 else None, "seconds": t_m,
+                    "energy_fp64_eval": evaluate(us, ws_, rho, m.PREC_F64),
+                    "energy_mixed_eval": evaluate(us, ws_, rho, prec)}
+    out["mixed"]["dE_eval_mixed_vs_fp64"] = abs(out["mixed"]["energy_mixed_eval"] - out["mixed"]["energy_fp64_eval"])
+    if args.scaling_k > 0:
+        d64 = scaling.scaling_dimensions(us[-1], ws_[-1], chi, k=args.scaling_k, prec=m.PREC_F64, tol=1e-10)
+        dmx = scaling.scaling_dimensions(us[-1], ws_[-1], chi, k=args.scaling_k, prec=prec, tol=1e-10)
+        out["mixed"]["scaling_dims_fp64"] = [float(x) for x in d64]
+        out["mixed"]["scaling_dims_max_abs_err"] = float(np.max(np.abs(d64 - dmx)))
+    if P > 0:
+        st, us, ws_, rho = fresh()
+        hist_p, t_p = run(st, [prec] * (S - P) + [m.PREC_F64] * P)
+        out["polish"] = {"sweep_energy_last": hist_p[-1], "seconds": t_p,
+                         "energy_fp64_eval": evaluate(us, ws_, rho, m.PREC_F64)}
+    if args.fp64_steps > 0:
+        st, us, ws_, rho = fresh()
+        hist_r, t_r = run(st, [m.PREC_F64] * S)
+        e_ref = evaluate(us, ws_, rho, m.PREC_F64)
+        out["ref_fp64"] = {"sweep_energy_last": hist_r[-1], "sweep_energy_change_last10": hist_r[-1] - hist_r[-11]
+                           if S > 10 else None, "seconds": t_r, "energy_fp64_eval": e_ref}
+        out["mixed"]["dE_vs_fp64_ground_state"] = abs(out["mixed"]["energy_fp64_eval"] - e_ref)
+        if P > 0:
+            out["polish"]["dE_vs_fp64_ground_state"] = abs(out["polish"]["energy_fp64_eval"] - e_ref)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = _args()
+    if args.slice_gib is not None and args.impl == "native":
+        import paper_1906_12030_gb300 as m
+        m.mera_set_slice_bytes(int(args.slice_gib * 2**30))
     if args.case == "batch":
         run_batch(args)
+        return
+    if args.case == "precision":
+        run_precision(args)
         return
     if args.case != "sweep":
         run_case(args)

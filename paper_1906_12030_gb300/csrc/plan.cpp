@@ -24,8 +24,7 @@ int elem_bytes(int prec) {
 int tc_block_n(int prec, int64_t N) {
   if (N > 128) return prec == PREC_BF16X6 ? 128 : 256;
   if (N > 64) return 128;
-  if (N > 32) return 64;
-  if (N > 16) return 32;
+  if (N > 16) return 64;
   return 16;
 }
 
@@ -236,7 +235,9 @@ struct Builder {
   std::vector<G> g;
   // Slicing of rank-7 intermediates: slice_leg[P2] = leg, sliced_child[P2] =
   // P1 (the producer, emitted inside P2's slice loop).
+  // slice_block[P2] = b: each slice covers b consecutive values of the leg.
   std::vector<int> slice_leg, sliced_child;
+  std::vector<int64_t> slice_block;
   std::vector<char> deferred;
   size_t slice_threshold = 0;
 
@@ -249,11 +250,14 @@ struct Builder {
     return s;
   }
 
-  LegMap legmap(const std::vector<int>& legs, const std::map<int, int64_t>& stride) const {
+  // Leg decomposition of a row or column index; leg `cut` (if any) has
+  // extent cut_dim instead of its full size (a slice block).
+  LegMap legmap(const std::vector<int>& legs, const std::map<int, int64_t>& stride, int cut = -1,
+                int64_t cut_dim = 0) const {
     LegMap m;
     m.n = int(legs.size());
     for (int i = 0; i < m.n; ++i) {
-      m.dim[i] = dim[legs[i]];
+      m.dim[i] = legs[i] == cut ? cut_dim : dim[legs[i]];
       m.stride[i] = stride.at(legs[i]);
     }
     return m;
@@ -281,11 +285,12 @@ struct Builder {
     return round_up(std::max<int64_t>(cols, 1), align);
   }
 
-  // One GEMM step for node i; with slice leg l >= 0 the step covers l = v
-  // only: the operand holding l is read from row block v (l is its
-  // outermost row leg), the sliced intermediate lives in a one-slice buffer,
-  // and the consumer writes its output at offset v * stride(l).
-  void emit_gemm(int i, int l, int64_t v, std::vector<int>& first_use, std::vector<int>& last_use) {
+  // One GEMM step for node i; with slice leg l >= 0 the step covers the
+  // values v*bl .. v*bl + bl - 1 of l only: the operand holding l is read
+  // from row block v (l is its outermost row leg), the sliced intermediate
+  // lives in a one-slice buffer, and the consumer writes its output at
+  // offset v * bl * stride(l).
+  void emit_gemm(int i, int l, int64_t v, int64_t bl, std::vector<int>& first_use, std::vector<int>& last_use) {
     const G& gi = g[i];
     Step s;
     s.kind = 1;
@@ -305,22 +310,20 @@ struct Builder {
     if (l >= 0) {
       const bool in_m = !ml.empty() && ml.front() == l;
       const bool in_n = !nl.empty() && nl.front() == l;
-      const int64_t dl = dim[l];
+      const int64_t ns = dim[l] / bl;  // number of slices
       // The producer reads row block v of its operand on l's side; the
       // consumer's operand on that side is the one-slice buffer itself.
       if (in_m) {
-        ml.erase(ml.begin());
-        gs.M /= dl;
+        gs.M /= ns;
         gs.a_off = is_producer ? v * gs.M * gs.lda : 0;
       } else if (in_n) {
-        nl.erase(nl.begin());
-        gs.N /= dl;
+        gs.N /= ns;
         gs.b_off = is_producer ? v * gs.N * gs.ldb : 0;
       }
-      gs.c_off = is_producer ? 0 : v * dst_stride[i].at(l);
+      gs.c_off = is_producer ? 0 : v * bl * dst_stride[i].at(l);
     }
-    gs.m_dst = legmap(ml, dst_stride[i]);
-    gs.n_dst = legmap(nl, dst_stride[i]);
+    gs.m_dst = legmap(ml, dst_stride[i], l, bl);
+    gs.n_dst = legmap(nl, dst_stride[i], l, bl);
     gs.alpha = (i == tr.root) ? alpha : 1.0;
     gs.accumulate = (i == tr.root) ? accumulate : 0;
     gs.flops = 2.0 * double(gs.M) * double(gs.N) * double(gs.K);
@@ -392,6 +395,7 @@ struct Builder {
     // that stays free in the consumer, the largest one.
     slice_leg.assign(nn, -1);
     sliced_child.assign(nn, -1);
+    slice_block.assign(nn, 1);
     deferred.assign(nn, 0);
     for (size_t i = 0; i < nn; ++i) {
       const Node& nd = tr.nodes[i];
@@ -406,7 +410,16 @@ struct Builder {
         for (int l : legs_list(cn.legs & ~K2))
           if (best < 0 || dim[l] > dim[best]) best = l;
         if (best < 0 || dim[best] < 2) continue;
+        // the largest block of the leg (a divisor of its size) whose slice
+        // stays within the threshold; whole slices keep the GEMMs large
+        int64_t bl = 1;
+        for (int64_t q = dim[best] - 1; q >= 1; --q)
+          if (dim[best] % q == 0 && bytes * double(q) / double(dim[best]) <= double(slice_threshold)) {
+            bl = q;
+            break;
+          }
         slice_leg[i] = best;
+        slice_block[i] = bl;
         sliced_child[i] = c;
         deferred[c] = 1;
         break;
@@ -491,7 +504,7 @@ struct Builder {
       for (int c : {gi.a, gi.b}) {
         Buffer b;
         b.rows = (c == gi.a) ? prod(mlegs) : prod(nlegs);
-        if (c == sliced_child[i]) b.rows /= dim[slice_leg[i]];  // one slice at a time
+        if (c == sliced_child[i]) b.rows = b.rows / dim[slice_leg[i]] * slice_block[i];  // one slice at a time
         b.ld = ld;
         b.plane_bytes = round_up(b.rows * ld * elem_bytes(prec), 256);
         b.bytes = b.plane_bytes * planes(prec);
@@ -545,13 +558,14 @@ struct Builder {
       }
       if (deferred[i]) continue;  // emitted inside its consumer's slice loop
       if (slice_leg[i] < 0) {
-        emit_gemm(i, -1, 0, first_use, last_use);
+        emit_gemm(i, -1, 0, 1, first_use, last_use);
         continue;
       }
       const int l = slice_leg[i];
-      for (int64_t v = 0; v < dim[l]; ++v) {
-        emit_gemm(sliced_child[i], l, v, first_use, last_use);
-        emit_gemm(i, l, v, first_use, last_use);
+      const int64_t bl = slice_block[i];
+      for (int64_t v = 0; v < dim[l] / bl; ++v) {
+        emit_gemm(sliced_child[i], l, v, bl, first_use, last_use);
+        emit_gemm(i, l, v, bl, first_use, last_use);
       }
     }
     double fmax = 0.0;

@@ -8,10 +8,13 @@
 //   warp 0      TMA producer (one elected lane), STAGES-deep ring shared by
 //               all of the CTA's tiles
 //   warp 1      tensor-memory allocator + MMA issuer (one lane)
-//   warps 2..9  epilogue: tcgen05.ld of the accumulator, convert, store; two
-//               warps per tensor-memory lane quarter, each taking half of the
-//               tile's columns; the accumulator is handed back to the MMA warp
-//               after the last load of all eight
+//   warps 2..17 epilogue: tcgen05.ld of the accumulator, convert, store; four
+//               warps per tensor-memory lane quarter, each taking a quarter of
+//               the tile's columns; the accumulator is handed back to the MMA
+//               warp after the last load of all sixteen.  At short K the
+//               epilogue, not the MMA, sets the pace, so it is written for
+//               few instructions per element: paired conversions and 32-bit
+//               column offsets when the destination allows them
 // Every mbarrier wait is bounded; a wait that gives up records
 // MERA_ETIMEOUT in a device status word, raises a CTA-wide abort flag, and
 // every role drains its copies in flight and leaves.
@@ -33,8 +36,9 @@ namespace {
 
 constexpr int kBM = 128;          // UMMA M (cta_group::1)
 constexpr int kSlabBytes = 128;   // one swizzle row: 64 BF16 or 32 TF32 along K
-constexpr int kThreads = 320;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreads = 64 + kEpiThreads;
 constexpr uint64_t kTimeoutNs = 2000000000ull;  // a wait longer than 2 s is a failure
 constexpr uint32_t kSpinCap = 1u << 30;            // second bound, independent of the timer
 
@@ -173,6 +177,7 @@ struct Epilogue {
   int split;        // K split: work item t covers output tile t % tiles and k-range t / tiles
   int kc;           // k-blocks per split
   float* partial;   // split > 1: raw FP32 partials [split][N][M], summed by splitk_reduce_kernel
+  int off32;        // every column offset n_dst(n) is below 2^31
 };
 
 template <int PREC, int BN>
@@ -187,8 +192,55 @@ struct Cfg {
   static constexpr int kAccCols = BN < 32 ? 32 : BN;     // one accumulator
   static constexpr int kTmemCols = 2 * kAccCols;            // two, double-buffered
   static constexpr uint32_t kFmt = (PREC == PREC_TF32) ? 2u : 1u;  // TF32 / BF16
-  static constexpr size_t kSmem = 1024 + size_t(kStages) * kStageBytes + 1024 + BN * sizeof(int64_t);
+  static constexpr size_t kSmem = 1024 + size_t(kStages) * kStageBytes + 1024 + BN * (sizeof(int64_t) + sizeof(int));
 };
+
+// One row's 32 accumulator values -> operand-format stores at row offset
+// off_m plus the 32-bit column offsets s_off[j] in shared memory (hi, lo /
+// hi, mid, lo planes
+// c_plane elements apart).  Conversions run on pairs (cvt.rn.bf16x2.f32);
+// each value is rounded exactly as the per-element path rounds it.
+template <int PREC>
+__device__ __forceinline__ void store_chunk(void* C, int64_t off_m, int64_t c_plane, const int* __restrict__ s_off,
+                                            const uint32_t (&v)[32]) {
+  if constexpr (PREC == PREC_TF32) {
+    float* r = static_cast<float*>(C) + off_m;
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+      const int4 q = *reinterpret_cast<const int4*>(s_off + j);
+      r[q.x] = round_tf32(__uint_as_float(v[j]));
+      r[q.y] = round_tf32(__uint_as_float(v[j + 1]));
+      r[q.z] = round_tf32(__uint_as_float(v[j + 2]));
+      r[q.w] = round_tf32(__uint_as_float(v[j + 3]));
+    }
+  } else {
+    __nv_bfloat16* r0 = static_cast<__nv_bfloat16*>(C) + off_m;
+    __nv_bfloat16* r1 = r0 + c_plane;
+    __nv_bfloat16* r2 = r1 + c_plane;
+#pragma unroll
+    for (int j = 0; j < 32; j += 2) {
+      const int2 q = *reinterpret_cast<const int2*>(s_off + j);
+      const int o[2] = {q.x, q.y};
+      const float f0 = __uint_as_float(v[j]), f1 = __uint_as_float(v[j + 1]);
+      const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+      r0[o[0]] = h.x;
+      r0[o[1]] = h.y;
+      if constexpr (PREC == PREC_BF16X3 || PREC == PREC_BF16X6) {
+        const float2 hf = __bfloat1622float2(h);
+        const float e0 = f0 - hf.x, e1 = f1 - hf.y;
+        const __nv_bfloat162 l = __floats2bfloat162_rn(e0, e1);
+        r1[o[0]] = l.x;
+        r1[o[1]] = l.y;
+        if constexpr (PREC == PREC_BF16X6) {
+          const float2 lf = __bfloat1622float2(l);
+          const __nv_bfloat162 q = __floats2bfloat162_rn(e0 - lf.x, e1 - lf.y);
+          r2[o[0]] = q.x;
+          r2[o[1]] = q.y;
+        }
+      }
+    }
+  }
+}
 
 template <int PREC, int BN>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -207,6 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_snapshot = abort_flag + 1;
   volatile int* never = abort_flag + 2;  // stays 0: waits that must not be cut short
   int64_t* off_n = reinterpret_cast<int64_t*>(aux + 1024);
+  int* off_n32 = reinterpret_cast<int*>(off_n + BN);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t tiles_n = (ep.N + BN - 1) / BN;
@@ -312,29 +365,32 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---- epilogue (warps 2..9) -------------------------------------------------
-    const int et = threadIdx.x - 64;  // 0..255
+    // ---- epilogue (warps 2..17) ------------------------------------------------
+    const int et = threadIdx.x - 64;  // 0..kEpiThreads-1
     const int quarter = warp % 4;     // tensor-memory lanes this warp may read
-    const int half = (warp - 2) / 4;  // which half of the tile's 32-column chunks
+    const int sub = (warp - 2) / 4;   // which quarter of the tile's 32-column chunks
+    constexpr int kSub = kEpiWarps / 4;
     const int row = quarter * 32 + lane;
     constexpr int kChunks = BN < 32 ? 1 : BN / 32;
-    const int ch_lo = kChunks == 1 ? (half == 0 ? 0 : 1) : half * (kChunks / 2);
-    const int ch_hi = kChunks == 1 ? 1 : (half + 1) * (kChunks / 2);
+    const int ch_lo = (sub * kChunks) / kSub, ch_hi = ((sub + 1) * kChunks) / kSub;
     const float alpha = float(ep.alpha);
+    const bool fast_ok = !ep.c_final && ep.split <= 1 && ep.off32 && ep.alpha == 1.0;
     uint32_t tc = 0;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++tc) {
       const int64_t mn = t % tiles_mn, ks = t / tiles_mn;
       const int64_t m0 = (mn / tiles_n) * kBM, n0 = (mn % tiles_n) * BN;
       const uint32_t b = tc & 1;
-      // all epilogue threads are done with the previous tile's off_n; decide
-      // together whether to go on
-      asm volatile("bar.sync 1, 256;" ::: "memory");
+      // all epilogue threads are done with the previous tile's offsets;
+      // decide together whether to go on
+      asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
       if (et == 0) *abort_snapshot = *abort_flag;
-      for (int c = et; c < BN; c += 256) {
+      for (int c = et; c < BN; c += kEpiThreads) {
         const int64_t n = n0 + c;
-        off_n[c] = n < ep.N ? legmap_offset32(ep.n_dst, uint32_t(n)) : 0;
+        const int64_t o = n < ep.N ? legmap_offset32(ep.n_dst, uint32_t(n)) : 0;
+        off_n[c] = o;
+        off_n32[c] = int(o);
       }
-      asm volatile("bar.sync 1, 256;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
       if (*abort_snapshot) break;
       const int64_t m = m0 + row;
       const bool row_ok = m < ep.M;
@@ -361,11 +417,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (!row_ok) continue;
         if (ep.split > 1) {  // raw partial sums, reduced in FP64 afterwards
+          float* p = ep.partial + (ks * ep.N + n0 + c0) * ep.M + m;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int64_t n = n0 + c0 + j;
-            if (c0 + j < BN && n < ep.N) ep.partial[(ks * ep.N + n) * ep.M + m] = __uint_as_float(v[j]);
-          }
+          for (int j = 0; j < 32; ++j, p += ep.M)
+            if (c0 + j < BN && n0 + c0 + j < ep.N) *p = __uint_as_float(v[j]);
+          continue;
+        }
+        if (fast_ok && c0 + 32 <= BN && n0 + c0 + 32 <= ep.N) {
+          // whole chunk, operand-format destination, offsets in 32 bits
+          store_chunk<PREC>(ep.C, off_m, ep.c_plane, off_n32 + c0, v);
           continue;
         }
 #pragma unroll
@@ -501,6 +561,13 @@ cudaError_t launch_cfg(const TcGemmArgs& a, cudaStream_t stream) {
   ep.split = split;
   ep.kc = int((num_k + split - 1) / split);
   ep.partial = a.partial;
+  {
+    // largest column offset, to allow 32-bit column offsets (the row
+    // offset stays 64-bit)
+    int64_t hi = 0;
+    for (int i = 0; i < a.n_dst.n; ++i) hi += (a.n_dst.dim[i] - 1) * a.n_dst.stride[i];
+    ep.off32 = hi < (int64_t(1) << 31) ? 1 : 0;
+  }
   if (split > 1 && (int64_t(split - 1) * ep.kc >= num_k)) return cudaErrorInvalidValue;  // empty split
   const int64_t tiles = ((a.M + kBM - 1) / kBM) * ((a.N + BN - 1) / BN) * split;
   if (tiles <= 0) return cudaErrorInvalidValue;
@@ -530,8 +597,7 @@ cudaError_t launch_prec(const TcGemmArgs& a, cudaStream_t stream) {
   // three-plane operands: a 256-wide B tile leaves room for one stage only
   if (a.N > 128 && PREC != PREC_BF16X6) return launch_cfg<PREC, (PREC == PREC_BF16X6 ? 128 : 256)>(a, stream);
   if (a.N > 64) return launch_cfg<PREC, 128>(a, stream);
-  if (a.N > 32) return launch_cfg<PREC, 64>(a, stream);
-  if (a.N > 16) return launch_cfg<PREC, 32>(a, stream);
+  if (a.N > 16) return launch_cfg<PREC, 64>(a, stream);  // (a 32-wide variant spilled registers)
   return launch_cfg<PREC, 16>(a, stream);
 }
 

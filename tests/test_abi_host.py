@@ -192,6 +192,23 @@ def forced_slicing():
 @pytest.mark.parametrize("prec,chi_b,chi_t", [(m.PREC_F64, 3, 3), (m.PREC_BF16X3, 2, 3), (m.PREC_F64, 4, 3),
                                               (m.PREC_BF16X6, 3, 5)])
 def test_sliced_programs_reproduce_oracle(forced_slicing, prec, chi_b, chi_t):
+    _check_sliced(prec, chi_b, chi_t)
+
+
+@pytest.mark.parametrize("prec", [m.PREC_F64, m.PREC_BF16X3])
+def test_block_sliced_programs_reproduce_oracle(prec):
+    """A threshold of half the intermediate makes each slice cover two values
+    of the sliced leg (chi = 4): the block form of the slice loop."""
+    eb = {m.PREC_F64: 8, m.PREC_BF16X3: 4}[prec]
+    m.mera_set_slice_bytes(4 ** 7 * eb // 2)
+    try:
+        n = _check_sliced(prec, 4, 4)
+    finally:
+        m.mera_set_slice_bytes(16 << 30)
+    assert n["ascend"] == 2 * 2 * 2  # 2 diagrams x 2 slices x (producer, consumer)
+
+
+def _check_sliced(prec, chi_b, chi_t):
     """Rank-7 intermediates computed one slice at a time (the memory plan
     that lets chi = 40 fit) still give the oracle's maps, and every diagram
     holding a chi^9 pair does slice it."""
@@ -204,12 +221,16 @@ def test_sliced_programs_reproduce_oracle(forced_slicing, prec, chi_b, chi_t):
              m.OP_DESCEND: ([None, rho, u, w], O.descend(rho, u, w)),
              m.OP_ENV_U: ([hs, rs, u, w], O.env_u(hs, rs, u, w)),
              m.OP_ENV_W: ([hs, rs, u, w], O.env_w(hs, rs, u, w))}
+    counts = {}
+    names = {m.OP_ASCEND: "ascend", m.OP_DESCEND: "descend", m.OP_ENV_U: "env_u", m.OP_ENV_W: "env_w"}
     for op, (inputs, want) in cases.items():
         plan = m.mera_plan_json(op, chi_b, chi_t, prec)
         sliced = [st for dg in plan["diagrams"] for st in dg["steps"] if st["kind"] == "gemm" and "=" in st["label"]]
         assert sliced, op
+        counts[names[op]] = len(sliced)
         got = _emulate(plan, inputs, want.size).reshape(want.shape)
         assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max()), op
+    return counts
 
 
 def test_slicing_shrinks_the_chi40_workspace():

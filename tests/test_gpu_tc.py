@@ -106,13 +106,16 @@ def test_maps_mixed_precision(prec, chi_b, chi_t):
 
 
 @pytest.mark.parametrize("prec", [m.PREC_F64, m.PREC_BF16X3, m.PREC_BF16])
-@pytest.mark.parametrize("chi_b,chi_t", [(4, 4), (8, 8), (4, 16)])
-def test_sliced_maps(prec, chi_b, chi_t):
+@pytest.mark.parametrize("chi_b,chi_t,block", [(4, 4, False), (8, 8, False), (4, 16, False), (8, 8, True)])
+def test_sliced_maps(prec, chi_b, chi_t, block):
     """Rank-7 intermediates computed one slice at a time (forced here at
     small chi; by default only above 16 GiB) give the oracle's maps within
-    the mode's tolerance, and agree with the unsliced program."""
+    the mode's tolerance, and agree with the unsliced program.  block: a
+    threshold of half the chi = 8 intermediate, so each slice covers four
+    values of the sliced leg."""
     whole = _maps(prec, chi_b, chi_t, 5)
-    m.mera_set_slice_bytes(0)
+    eb = {m.PREC_F64: 8, m.PREC_BF16X3: 4, m.PREC_BF16: 2}[prec]
+    m.mera_set_slice_bytes(8 ** 7 * eb // 2 if block else 0)
     try:
         plan = m.mera_plan_json(m.OP_ENV_W, chi_b, chi_t, prec)
         assert any("=" in st["label"] for dg in plan["diagrams"] for st in dg["steps"] if st["kind"] == "gemm")

@@ -128,7 +128,7 @@ struct Arena {
 };
 
 // Execute a contraction program; inputs[slot] are device pointers.
-// reuse_resident: the u/w operand copies left by the previous run of this
+// reuse_resident: the u/w operand copies (resident == 1) left by the previous run of this
 // same program (same u, w, workspace) are still valid; skip those copies.
 mera_status run_program(const OpProgram& prog, const double* const inputs[4], double* out, int prec, char* ws,
                         cudaStream_t stream, bool reuse_resident = false) {
@@ -137,7 +137,7 @@ mera_status run_program(const OpProgram& prog, const double* const inputs[4], do
       if (st.kind == 0) {
         const PermuteStep& p = st.p;
         const Buffer& b = dg.bufs[p.dst_buf];
-        if (reuse_resident && b.resident) continue;
+        if (p.skip || (reuse_resident && b.resident == 1)) continue;
         const int64_t plane = b.plane_bytes / elem_bytes(prec);
         ProfScope ps(stream, 1, 0, 0.0);
         cudaError_t e = launch_permute(p, inputs[p.slot], ws + b.offset, plane, prec, stream);

@@ -1,6 +1,9 @@
 // Binary64 kernels: operand permute/cast, FP64 GEMM with scattered epilogue,
 // deterministic reductions (trace, Hilbert-Schmidt products, norms) and the
 // elementwise parts of the Newton-Schulz polar iteration.
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -9,20 +12,24 @@ namespace mera {
 // ---------------------------------------------------------------------------
 // Input tensor -> operand layout, cast to the operand precision.
 //
-// The copy is a permutation of the tensor's legs.  Let `a` be the leg that is
-// contiguous in the destination and `b` the leg contiguous in the source.
-// When a != b, 32 x 32 tiles over (a, b) go through shared memory so that the
-// reads run along b and the writes along a, both coalesced; when a == b the
-// copy runs along that leg directly.  The offsets of the remaining legs are
-// decoded once per tile.
+// The copy is a permutation of the tensor's legs.  The legs are grouped into
+// A (those of smallest destination stride, up to kTile elements), B (those of
+// smallest source stride among the rest, up to kTile elements) and the outer
+// legs; a leg is split in two where that makes a group fill exactly.  Each
+// block moves TA x TB tiles through shared memory: reads run along B (or
+// along A when A is also contiguous in the source), writes along A, so both
+// sides move runs of up to kTile elements.  The in-tile offsets come from
+// tables in shared memory and the outer offsets are decoded once per tile.
 // ---------------------------------------------------------------------------
+constexpr int kTile = 64;
+
 struct PermuteArgs {
   int n_other;
-  int64_t dim[kMaxLeg], src_stride[kMaxLeg], dst_stride[kMaxLeg];  // legs other than a, b
-  int64_t da, db;          // sizes of legs a and b
-  int64_t a_src, a_dst;    // strides of leg a (a_dst is 1 unless every leg is degenerate)
-  int64_t b_src, b_dst;    // strides of leg b (b_src is 1 likewise)
-  int64_t outer;           // product of the other legs' sizes
+  int64_t dim[2 * kMaxLeg], src_stride[2 * kMaxLeg], dst_stride[2 * kMaxLeg];  // outer legs
+  int ta, tb;              // tile extents (products of the A and B legs)
+  int read_a;              // A is contiguous in the source too: read along A
+  int64_t outer;           // number of tiles (product of the outer legs)
+  int64_t a_src[kTile], a_dst[kTile], b_src[kTile], b_dst[kTile];  // in-tile offsets
 };
 
 // o < 2^31 (checked at launch), so the decode divides in 32 bits.
@@ -40,47 +47,27 @@ __device__ __forceinline__ void decode_other(const PermuteArgs& p, uint32_t o, i
   }
 }
 
-constexpr int kPermuteTile = 4352;  // doubles of shared memory per block (34.8 KB)
-
-// Tiles of TA x TB (a, b) elements, TA, TB <= 32; several tiles (consecutive
-// outer indices) per block pass so that a pass moves up to 1024 elements.
-// Each thread's in-tile coordinates are fixed for the whole kernel and each
-// tile's base offsets and extents are decoded once into shared memory, so
-// the element loops do no division.  read_a_fast: the source is contiguous
-// along a as well (a == b case, b is then another leg), so reads run along a.
 template <int PREC>
 __global__ void __launch_bounds__(256) permute_tile_kernel(const double* __restrict__ src, void* dst, int64_t plane,
-                                                           const __grid_constant__ PermuteArgs p, int read_a_fast) {
-  __shared__ double tile[kPermuteTile];
-  __shared__ int64_t s_src[64], s_dst[64];
-  __shared__ int s_alim[64], s_blim[64];
-  const int TA = int(p.da < 32 ? p.da : 32), TB = int(p.db < 32 ? p.db : 32);
-  const int per_tile = TA * TB;
-  const int cap = kPermuteTile / (TA * (TB + 1));
-  const int nb = cap < 64 ? cap : 64;  // tiles per pass (up to ~4096 elements)
-  const uint32_t ca = uint32_t((p.da + TA - 1) / TA), cb = uint32_t((p.db + TB - 1) / TB);
-  const int64_t total = p.outer * ca * cb;
+                                                           const __grid_constant__ PermuteArgs p) {
+  __shared__ double tile[kTile * (kTile + 1)];
+  __shared__ int64_t s_as[kTile], s_ad[kTile], s_bs[kTile], s_bd[kTile];
   const int tid = threadIdx.x;
-  const int tstride = TA * (TB + 1);
-  for (int64_t t0 = int64_t(blockIdx.x) * nb; t0 < total; t0 += int64_t(gridDim.x) * nb) {
-    const int ntiles = int(total - t0 < nb ? total - t0 : nb);
-    if (tid < ntiles) {
-      const uint32_t t = uint32_t(t0 + tid);
-      const uint32_t o = t / (ca * cb);
-      const uint32_t rem = t - o * ca * cb;
-      const int64_t a0 = int64_t(rem / cb) * TA, b0 = int64_t(rem % cb) * TB;
-      int64_t so, dof;
-      decode_other(p, o, so, dof);
-      s_src[tid] = so + a0 * p.a_src + b0 * p.b_src;
-      s_dst[tid] = dof + a0 * p.a_dst + b0 * p.b_dst;
-      s_alim[tid] = int(p.da - a0 < TA ? p.da - a0 : TA);
-      s_blim[tid] = int(p.db - b0 < TB ? p.db - b0 : TB);
-    }
-    __syncthreads();
-    const int count = ntiles * per_tile;
-    // x / d for x <= 2^22 by a float reciprocal: (x + 0.5) / d is at least
-    // 0.5 / d away from an integer, far more than the float rounding error
-    const float inv_pt = 1.0f / float(per_tile), inv_ta = 1.0f / float(TA), inv_tb = 1.0f / float(TB);
+  const int ta = p.ta, tb = p.tb, count = ta * tb;
+  if (tid < kTile) {
+    s_as[tid] = tid < ta ? p.a_src[tid] : 0;
+    s_ad[tid] = tid < ta ? p.a_dst[tid] : 0;
+    s_bs[tid] = tid < tb ? p.b_src[tid] : 0;
+    s_bd[tid] = tid < tb ? p.b_dst[tid] : 0;
+  }
+  __syncthreads();
+  // x / d for x < 2^13 by a float reciprocal: (x + 0.5) / d is at least
+  // 0.5 / d away from an integer, far more than the float rounding error
+  const float inv_ta = 1.0f / float(ta), inv_tb = 1.0f / float(tb);
+  const int pitch = tb + 1;  // tile[ia * pitch + ib]
+  for (int64_t t = blockIdx.x; t < p.outer; t += gridDim.x) {
+    int64_t so, dof;
+    decode_other(p, uint32_t(t), so, dof);
     // reads: 8 independent loads per thread in flight before any shared store
     for (int e0 = 0; e0 < count; e0 += 256 * 8) {
       double v[8];
@@ -91,19 +78,16 @@ __global__ void __launch_bounds__(256) permute_tile_kernel(const double* __restr
         slot[k] = -1;
         v[k] = 0.0;
         if (e < count) {
-          const int j = int((float(e) + 0.5f) * inv_pt), r = e - j * per_tile;
           int ia, ib;
-          if (read_a_fast) {
-            ib = int((float(r) + 0.5f) * inv_ta);
-            ia = r - ib * TA;
+          if (p.read_a) {
+            ib = int((float(e) + 0.5f) * inv_ta);
+            ia = e - ib * ta;
           } else {
-            ia = int((float(r) + 0.5f) * inv_tb);
-            ib = r - ia * TB;
+            ia = int((float(e) + 0.5f) * inv_tb);
+            ib = e - ia * tb;
           }
-          if (ia < s_alim[j] && ib < s_blim[j]) {
-            v[k] = src[s_src[j] + ia * p.a_src + ib * p.b_src];
-            slot[k] = j * tstride + ia * (TB + 1) + ib;
-          }
+          v[k] = src[so + s_as[ia] + s_bs[ib]];
+          slot[k] = ia * pitch + ib;
         }
       }
 #pragma unroll
@@ -111,83 +95,121 @@ __global__ void __launch_bounds__(256) permute_tile_kernel(const double* __restr
         if (slot[k] >= 0) tile[slot[k]] = v[k];
     }
     __syncthreads();
-    // writes along a (contiguous in the destination)
+    // writes along A (contiguous in the destination)
     for (int e = tid; e < count; e += 256) {
-      const int j = int((float(e) + 0.5f) * inv_pt), r = e - j * per_tile;
-      const int ib = int((float(r) + 0.5f) * inv_ta), ia = r - ib * TA;
-      if (ia < s_alim[j] && ib < s_blim[j])
-        OperandStore<PREC>::store(dst, s_dst[j] + ib * p.b_dst + ia * p.a_dst, plane,
-                                  tile[j * tstride + ia * (TB + 1) + ib]);
+      const int ib = int((float(e) + 0.5f) * inv_ta), ia = e - ib * ta;
+      OperandStore<PREC>::store(dst, dof + s_ad[ia] + s_bd[ib], plane, tile[ia * pitch + ib]);
     }
     __syncthreads();
   }
 }
 
+namespace {
+
+struct Leg {
+  int64_t dim, ss, ds;
+};
+
+// Take legs from `pool` in order of `key` into a group of at most kTile
+// elements; the first leg that does not fit whole is split when a divisor
+// of its size fills the group further.  Returns the group's legs, inner first.
+template <typename Key>
+std::vector<Leg> take_group(std::vector<Leg>& pool, Key key) {
+  std::stable_sort(pool.begin(), pool.end(), [&](const Leg& x, const Leg& y) { return key(x) < key(y); });
+  std::vector<Leg> g;
+  int64_t prod = 1;
+  while (!pool.empty()) {
+    Leg l = pool.front();
+    if (prod * l.dim <= kTile) {
+      g.push_back(l);
+      prod *= l.dim;
+      pool.erase(pool.begin());
+      continue;
+    }
+    int64_t q = kTile / prod;
+    while (q > 1 && l.dim % q) --q;
+    if (q > 1) {  // inner part (q values) joins the group, outer part stays
+      g.push_back({q, l.ss, l.ds});
+      pool.front() = {l.dim / q, l.ss * q, l.ds * q};
+      prod *= q;
+    }
+    break;
+  }
+  return g;
+}
+
+// In-tile offsets of a group: index i = sum over legs of x_leg * (product
+// of the inner legs' sizes), inner leg fastest.
+int fill_table(const std::vector<Leg>& g, int64_t* src_off, int64_t* dst_off) {
+  int n = 1;
+  src_off[0] = dst_off[0] = 0;
+  for (const Leg& l : g) {
+    for (int64_t x = 1; x < l.dim; ++x)
+      for (int i = 0; i < n; ++i) {
+        src_off[x * n + i] = src_off[i] + x * l.ss;
+        dst_off[x * n + i] = dst_off[i] + x * l.ds;
+      }
+    n *= int(l.dim);
+  }
+  return n;
+}
+
+}  // namespace
+
 cudaError_t launch_permute(const PermuteStep& st, const double* src, void* dst, int64_t plane_elems,
                            int prec, cudaStream_t stream) {
   if (st.rows <= 0 || st.cols <= 0) return cudaSuccess;
-  // Every leg with its source and destination strides.
-  int n = 0;
-  int64_t dim[2 * kMaxLeg], ss[2 * kMaxLeg], ds[2 * kMaxLeg];
+  // Every leg with its source and destination strides (size-1 legs dropped).
+  std::vector<Leg> pool;
   int64_t acc = st.ld;
   for (int i = st.row_src.n - 1; i >= 0; --i) {
-    dim[n] = st.row_src.dim[i];
-    ss[n] = st.row_src.stride[i];
-    ds[n] = acc;
-    acc *= dim[n];
-    ++n;
+    if (st.row_src.dim[i] > 1) pool.push_back({st.row_src.dim[i], st.row_src.stride[i], acc});
+    acc *= st.row_src.dim[i];
   }
   acc = 1;
   for (int i = st.col_src.n - 1; i >= 0; --i) {
-    dim[n] = st.col_src.dim[i];
-    ss[n] = st.col_src.stride[i];
-    ds[n] = acc;
-    acc *= dim[n];
-    ++n;
+    if (st.col_src.dim[i] > 1) pool.push_back({st.col_src.dim[i], st.col_src.stride[i], acc});
+    acc *= st.col_src.dim[i];
   }
-  // a: smallest destination stride, b: smallest source stride (legs of size
-  // 1 are skipped unless every leg has size 1).
-  int a = 0, b = 0;
-  for (int i = 1; i < n; ++i) {
-    const bool ai = dim[i] > 1, aa = dim[a] > 1;
-    if ((ai && !aa) || (ai == aa && ds[i] < ds[a])) a = i;
-    if ((ai && !(dim[b] > 1)) || (ai == (dim[b] > 1) && ss[i] < ss[b])) b = i;
-  }
-  // a == b: tile over (a, b2) with b2 the leg of next-smallest source
-  // stride; reads then run along a too.  A tensor with one non-trivial leg
-  // gets a dummy b of size 1.
-  int read_a_fast = 0;
-  if (a == b) {
-    read_a_fast = 1;
-    b = -1;
-    for (int i = 0; i < n; ++i)
-      if (i != a && dim[i] > 1 && (b < 0 || ss[i] < ss[b])) b = i;
-  }
+  // Ls: the leg contiguous in the source, Ld: the one contiguous in the
+  // destination.  When they differ, Ls is kept out of A so that it leads B;
+  // when they coincide, A leads with it and the reads run along A.
   PermuteArgs p{};
-  p.da = dim[a];
-  p.db = b >= 0 ? dim[b] : 1;
-  p.a_src = ss[a];
-  p.a_dst = ds[a];
-  p.b_src = b >= 0 ? ss[b] : 0;
-  p.b_dst = b >= 0 ? ds[b] : 0;
+  std::vector<Leg> ga, gb;
+  if (!pool.empty()) {
+    size_t is = 0, id = 0;
+    for (size_t i = 1; i < pool.size(); ++i) {
+      if (pool[i].ss < pool[is].ss) is = i;
+      if (pool[i].ds < pool[id].ds) id = i;
+    }
+    if (is == id) {
+      p.read_a = 1;
+      ga = take_group(pool, [](const Leg& l) { return l.ds; });
+      gb = take_group(pool, [](const Leg& l) { return l.ss; });
+    } else {
+      const Leg ls = pool[is];
+      pool.erase(pool.begin() + long(is));
+      ga = take_group(pool, [](const Leg& l) { return l.ds; });
+      pool.push_back(ls);
+      gb = take_group(pool, [](const Leg& l) { return l.ss; });
+    }
+  }
+  p.ta = fill_table(ga, p.a_src, p.a_dst);
+  p.tb = fill_table(gb, p.b_src, p.b_dst);
+  if (int(pool.size()) > 2 * kMaxLeg) return cudaErrorInvalidValue;
   p.outer = 1;
-  // other legs, outermost first (order is irrelevant for correctness)
-  for (int i = n - 1; i >= 0; --i) {
-    if (i == a || i == b) continue;
-    if (p.n_other >= kMaxLeg) return cudaErrorInvalidValue;
-    p.dim[p.n_other] = dim[i];
-    p.src_stride[p.n_other] = ss[i];
-    p.dst_stride[p.n_other] = ds[i];
-    p.outer *= dim[i];
+  p.n_other = 0;
+  for (const Leg& l : pool) {  // outer legs (order is irrelevant for correctness)
+    p.dim[p.n_other] = l.dim;
+    p.src_stride[p.n_other] = l.ss;
+    p.dst_stride[p.n_other] = l.ds;
+    p.outer *= l.dim;
     ++p.n_other;
   }
+  if (p.outer >= (int64_t(1) << 31)) return cudaErrorInvalidValue;  // 32-bit tile indices
   count_launch();
-  const int64_t ta = std::min<int64_t>(p.da, 32), tb = std::min<int64_t>(p.db, 32);
-  const int64_t work = p.outer * ((p.da + ta - 1) / ta) * ((p.db + tb - 1) / tb);
-  const int64_t per_pass = std::min<int64_t>(std::max<int64_t>(kPermuteTile / (ta * (tb + 1)), 1), 64);
-  if (work >= (int64_t(1) << 31)) return cudaErrorInvalidValue;  // 32-bit tile indices
-  const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>((work + per_pass - 1) / per_pass, 152 * 16)));
-#define MERA_PERMUTE_LAUNCH(P) permute_tile_kernel<P><<<grid, 256, 0, stream>>>(src, dst, plane_elems, p, read_a_fast);
+  const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(p.outer, 152 * 8)));
+#define MERA_PERMUTE_LAUNCH(P) permute_tile_kernel<P><<<grid, 256, 0, stream>>>(src, dst, plane_elems, p);
   switch (prec) {
     case PREC_F64: MERA_PERMUTE_LAUNCH(PREC_F64) break;
     case PREC_TF32: MERA_PERMUTE_LAUNCH(PREC_TF32) break;
@@ -406,29 +428,48 @@ __global__ void __launch_bounds__(1024) trace_kernel(const double* __restrict__ 
   if (threadIdx.x == 0) *out = v;
 }
 
+// rho = (X + X^T) / (2 tr X) over pairs of 32 x 32 tiles (I, J), I <= J:
+// both tiles are read once and both written once, so X is read once in all.
 template <bool RESID>
 __global__ void __launch_bounds__(256) sym_normalize_kernel(const double* __restrict__ X, double* rho, int64_t n,
                                                             const double* __restrict__ trace, double* partials) {
-  __shared__ double xt[32][33];
+  __shared__ double sa[32][33], sb[32][33];
   const double inv2t = 0.5 / *trace;
   const int64_t nt = (n + 31) / 32;
   double v = 0.0;
   for (int64_t t = blockIdx.x; t < nt * nt; t += gridDim.x) {
-    const int64_t i0 = (t / nt) * 32, j0 = (t % nt) * 32;
+    const int64_t I = t / nt, J = t % nt;
+    if (I > J) continue;  // uniform over the block
+    const int64_t i0 = I * 32, j0 = J * 32;
     for (int r = threadIdx.y; r < 32; r += 8) {
-      const int64_t gj = j0 + r, gi = i0 + threadIdx.x;
-      xt[threadIdx.x][r] = (gj < n && gi < n) ? X[gj * n + gi] : 0.0;
+      const int64_t ga = i0 + r, gb = j0 + threadIdx.x;  // tile (I, J)
+      sa[r][threadIdx.x] = (ga < n && gb < n) ? X[ga * n + gb] : 0.0;
+      const int64_t gc = j0 + r, gd = i0 + threadIdx.x;  // tile (J, I)
+      sb[r][threadIdx.x] = (gc < n && gd < n) ? X[gc * n + gd] : 0.0;
     }
     __syncthreads();
     for (int r = threadIdx.y; r < 32; r += 8) {
-      const int64_t gi = i0 + r, gj = j0 + threadIdx.x;
-      if (gi < n && gj < n) {
-        const double nv = (X[gi * n + gj] + xt[r][threadIdx.x]) * inv2t;
-        if constexpr (RESID) {
-          const double d = nv - rho[gi * n + gj];
-          v += d * d;
+      {
+        const int64_t gi = i0 + r, gj = j0 + threadIdx.x;
+        if (gi < n && gj < n) {
+          const double nv = (sa[r][threadIdx.x] + sb[threadIdx.x][r]) * inv2t;
+          if constexpr (RESID) {
+            const double d = nv - rho[gi * n + gj];
+            v += d * d;
+          }
+          rho[gi * n + gj] = nv;
         }
-        rho[gi * n + gj] = nv;
+      }
+      if (I != J) {
+        const int64_t gi = j0 + r, gj = i0 + threadIdx.x;
+        if (gi < n && gj < n) {
+          const double nv = (sb[r][threadIdx.x] + sa[threadIdx.x][r]) * inv2t;
+          if constexpr (RESID) {
+            const double d = nv - rho[gi * n + gj];
+            v += d * d;
+          }
+          rho[gi * n + gj] = nv;
+        }
       }
     }
     __syncthreads();

@@ -7,6 +7,7 @@
 #include <functional>
 #include <limits>
 #include <map>
+#include <set>
 #include <memory>
 #include <mutex>
 #include <sstream>
@@ -33,7 +34,7 @@ int tc_split_k(int prec, int64_t M, int64_t N, int64_t K) {
   constexpr int64_t kSMs = 152;
   const int64_t bn = tc_block_n(prec, N);
   const int64_t tiles = ((M + 127) / 128) * ((N + bn - 1) / bn);
-  const int64_t bk = 128 / elem_bytes(prec);
+  const int64_t bk = 128 / elem_bytes(prec);  // K per stage of the GEMM kernel
   const int64_t num_k = (K + bk - 1) / bk;
   if (tiles >= kSMs || num_k < 8) return 1;
   int64_t s = std::min<int64_t>((2 * kSMs + tiles - 1) / tiles, num_k / 4);
@@ -215,6 +216,18 @@ std::string legs_str(const std::vector<int>& v) {
 
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// Identity of an input copy: which input, and where each of its elements
+// goes.  Two steps with the same key write the same bytes.
+std::string permute_key(const PermuteStep& p) {
+  std::ostringstream o;
+  o << p.slot << ':' << p.rows << 'x' << p.cols << '/' << p.ld;
+  for (const LegMap* m : {&p.row_src, &p.col_src}) {
+    o << '|';
+    for (int i = 0; i < m->n; ++i) o << m->dim[i] << '@' << m->stride[i] << ',';
+  }
+  return o.str();
+}
+
 struct Builder {
   const Diagram& dg;
   const int64_t* dim;
@@ -240,9 +253,13 @@ struct Builder {
   std::vector<int64_t> slice_block;
   std::vector<char> deferred;
   size_t slice_threshold = 0;
+  // Copies of h or rho that several diagrams of the operation read in the
+  // same layout (keys of permute_key): kept outside the arena.
+  const std::set<std::string>* shared = nullptr;
 
-  Builder(const Diagram& d, const int64_t* dm, int p, double al, int acc, size_t sb)
-      : dg(d), dim(dm), prec(p), alpha(al), accumulate(acc), slice_threshold(sb) {}
+  Builder(const Diagram& d, const int64_t* dm, int p, double al, int acc, size_t sb,
+          const std::set<std::string>* sh = nullptr)
+      : dg(d), dim(dm), prec(p), alpha(al), accumulate(acc), slice_threshold(sb), shared(sh) {}
 
   int64_t prod(const std::vector<int>& legs) const {
     int64_t s = 1;
@@ -553,7 +570,10 @@ struct Builder {
         prog.steps.push_back(s);
         const int si = int(prog.steps.size()) - 1;
         first_use[p.dst_buf] = si;
-        if (ts.slot == SLOT_U || ts.slot == SLOT_W) prog.bufs[p.dst_buf].resident = 1;
+        if (ts.slot == SLOT_U || ts.slot == SLOT_W)
+          prog.bufs[p.dst_buf].resident = 1;
+        else if (shared && shared->count(permute_key(p)))
+          prog.bufs[p.dst_buf].resident = 2;
         continue;
       }
       if (deferred[i]) continue;  // emitted inside its consumer's slice loop
@@ -635,21 +655,69 @@ const OpProgram* get_program(int op, int chi_b, int chi_t, int prec) {
   int64_t dim[64];
   for (int l = 0; l < 64; ++l) dim[l] = chi_b;
   for (char c : std::string("pqrstv")) dim[label_id(c)] = chi_t;
-  auto prog = std::make_unique<OpProgram>();
   const std::vector<Diagram> ds = diagrams_of(op);
-  for (size_t d = 0; d < ds.size(); ++d) {
-    Builder b(ds[d], dim, prec, 0.5, d == 0 ? 0 : 1, g_slice_bytes);
-    if (!b.build()) return nullptr;
-    prog->flops += b.prog.flops;
-    prog->diagrams.push_back(std::move(b.prog));
+  auto build_all = [&](const std::set<std::string>* sh) -> std::unique_ptr<OpProgram> {
+    auto pr = std::make_unique<OpProgram>();
+    for (size_t d = 0; d < ds.size(); ++d) {
+      Builder b(ds[d], dim, prec, 0.5, d == 0 ? 0 : 1, g_slice_bytes, sh);
+      if (!b.build()) return nullptr;
+      pr->flops += b.prog.flops;
+      pr->diagrams.push_back(std::move(b.prog));
+    }
+    return pr;
+  };
+  auto prog = build_all(nullptr);
+  if (!prog) return nullptr;
+  // Copies of h or rho made more than once in the same layout are made once
+  // and kept for the whole call, as long as they are small (each at most
+  // 1 GiB, 4 GiB in all): at large chi a copy costs nothing next to the
+  // chi^9 work, while keeping it would cost HBM.
+  {
+    std::map<std::string, int> count;
+    std::map<std::string, int64_t> bytes;
+    std::vector<std::string> order;
+    for (const Program& pg : prog->diagrams)
+      for (const Step& st : pg.steps)
+        if (st.kind == 0 && (st.p.slot == SLOT_OP || st.p.slot == SLOT_RHO)) {
+          const std::string k = permute_key(st.p);
+          if (count[k]++ == 0) order.push_back(k);
+          bytes[k] = pg.bufs[st.p.dst_buf].bytes;
+        }
+    std::set<std::string> shared;
+    int64_t budget = int64_t(4) << 30;
+    for (const std::string& k : order)
+      if (count[k] > 1 && bytes[k] <= (int64_t(1) << 30) && bytes[k] <= budget) {
+        shared.insert(k);
+        budget -= bytes[k];
+      }
+    if (!shared.empty()) {
+      prog = build_all(&shared);
+      if (!prog) return nullptr;
+    }
   }
-  // Workspace: [resident copies of diagram 0 | diagram 1 | ...][transient arena]
+  // Workspace: [resident copies, one per distinct copy][transient arena].
+  // A later step making a copy that already exists is skipped.
   size_t res_base = 0;
-  for (Program& pg : prog->diagrams) {
-    for (Buffer& bf : pg.bufs)
-      if (bf.resident) bf.offset += int64_t(res_base);
-    res_base += (pg.resident_bytes + 255) / 256 * 256;
+  {
+    std::map<std::string, int64_t> made;  // key -> offset
+    for (Program& pg : prog->diagrams)
+      for (Step& st : pg.steps) {
+        if (st.kind != 0) continue;
+        Buffer& bf = pg.bufs[st.p.dst_buf];
+        if (!bf.resident) continue;
+        const std::string k = permute_key(st.p);
+        auto it = made.find(k);
+        if (it != made.end()) {
+          bf.offset = it->second;
+          st.p.skip = 1;
+        } else {
+          bf.offset = int64_t(res_base);
+          made[k] = bf.offset;
+          res_base += size_t(bf.bytes + 255) / 256 * 256;
+        }
+      }
   }
+  prog->persistent_bytes = res_base;
   size_t trans = 0;
   for (Program& pg : prog->diagrams) {
     for (Buffer& bf : pg.bufs)
@@ -685,7 +753,7 @@ std::string program_json(const OpProgram& prog, int op, int chi_b, int chi_t, in
   };
   o << "{\"op\":" << op << ",\"chi_b\":" << chi_b << ",\"chi_t\":" << chi_t << ",\"prec\":" << prec
     << ",\"ws_bytes\":" << prog.ws_bytes << ",\"flops\":" << prog.flops << ",\"elem_bytes\":" << elem_bytes(prec)
-    << ",\"planes\":" << planes(prec) << ",\"diagrams\":[";
+    << ",\"planes\":" << planes(prec) << ",\"persistent_bytes\":" << prog.persistent_bytes << ",\"diagrams\":[";
   for (size_t d = 0; d < prog.diagrams.size(); ++d) {
     const Program& p = prog.diagrams[d];
     o << (d ? "," : "") << "{\"ws_bytes\":" << p.ws_bytes << ",\"flops\":" << p.flops << ",\"bufs\":[";
@@ -699,7 +767,8 @@ std::string program_json(const OpProgram& prog, int op, int chi_b, int chi_t, in
       o << (s ? "," : "");
       if (st.kind == 0) {
         o << "{\"kind\":\"permute\",\"slot\":" << st.p.slot << ",\"dst_buf\":" << st.p.dst_buf
-          << ",\"rows\":" << st.p.rows << ",\"cols\":" << st.p.cols << ",\"ld\":" << st.p.ld << ",\"row_src\":";
+          << ",\"rows\":" << st.p.rows << ",\"cols\":" << st.p.cols << ",\"ld\":" << st.p.ld
+          << ",\"skip\":" << st.p.skip << ",\"row_src\":";
         lm(st.p.row_src);
         o << ",\"col_src\":";
         lm(st.p.col_src);

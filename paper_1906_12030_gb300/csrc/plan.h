@@ -37,6 +37,7 @@ struct PermuteStep {
   int slot = 0;
   int dst_buf = 0;
   int64_t rows = 0, cols = 0, ld = 0;
+  int skip = 0;  // an earlier step of the same call already made this copy
   LegMap row_src, col_src;
 };
 
@@ -69,7 +70,10 @@ struct Buffer {
   int64_t offset = 0;         // byte offset in the workspace
   int64_t plane_bytes = 0;    // bytes of one plane (BF16X3 keeps hi, then lo)
   int64_t bytes = 0;          // plane_bytes * planes
-  int resident = 0;           // copy of a disentangler/isometry: kept for the whole call
+  int resident = 0;           // kept for the whole call, outside the transient arena:
+                              // 1 copy of a disentangler/isometry (a later call with the
+                              // same u, w may reuse it), 2 copy of h or rho that several
+                              // diagrams read in the same layout
 };
 
 // The program of one diagram.  Buffers are laid out in one arena.
@@ -87,6 +91,7 @@ struct Program {
 struct OpProgram {
   std::vector<Program> diagrams;
   size_t ws_bytes = 0;
+  size_t persistent_bytes = 0;  // leading workspace bytes holding the resident copies
   double flops = 0.0;
 };
 

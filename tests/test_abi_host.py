@@ -113,8 +113,14 @@ def _emulate(plan, inputs, out_size):
                 assert b["bytes"] >= b["rows"] * b["ld"] * 4
             else:
                 assert b["ld"] * eb % 16 == 0  # TMA: row pitch multiple of 16 bytes
-        arena[:] = np.nan  # stale data from an earlier diagram must never be read
+        # stale data from an earlier diagram must never be read, except the
+        # copies kept for the whole call (the leading persistent bytes)
+        arena[plan["persistent_bytes"] // eb:] = np.nan
         for st in dg["steps"]:
+            if st["kind"] == "permute" and st["skip"]:
+                b = bufs[st["dst_buf"]]
+                assert b["resident"] and b["offset"] + b["bytes"] <= plan["persistent_bytes"]
+                continue  # the same copy was made by an earlier step
             if st["kind"] == "permute":
                 src = inputs[st["slot"]].reshape(-1)
                 b = bufs[st["dst_buf"]]
@@ -267,17 +273,44 @@ def test_split_k_partials_do_not_overlap_live_buffers():
 @pytest.mark.parametrize("op", [m.OP_DESCEND, m.OP_ENV_W])
 def test_resident_operand_copies_are_never_reused(op):
     """The operand copies of u and w are kept for the whole call (the fixed
-    point reuses them across its power steps): they must not overlap each
-    other, in any diagram, nor any transient buffer."""
+    point reuses them across its power steps), and so are copies of h or rho
+    that several diagrams read in the same layout: distinct copies must not
+    overlap each other, in any diagram, nor any transient buffer."""
     plan = m.mera_plan_json(op, 4, 4, m.PREC_BF16X3)
     resident, transient = [], []
     for dg in plan["diagrams"]:
         for b in dg["bufs"]:
             (resident if b["resident"] else transient).append((b["offset"], b["offset"] + b["bytes"]))
     assert resident
-    resident.sort()
+    resident = sorted(set(resident))  # a copy shared by several diagrams appears once
     for (a0, a1), (b0, b1) in zip(resident, resident[1:]):
         assert a1 <= b0
     for r0, r1 in resident:
         for t0, t1 in transient:
             assert r1 <= t0 or t1 <= r0
+
+
+@pytest.mark.parametrize("op,chi", [(m.OP_DESCEND, 16), (m.OP_ENV_W, 16), (m.OP_ENV_U, 8)])
+def test_identical_input_copies_are_made_once(op, chi):
+    """Each distinct operand copy of an input is made once per call; every
+    later step that would make the same copy is skipped and reads the first
+    one (the emulation of these programs against the oracle covers the
+    correctness; this checks the count)."""
+    plan = m.mera_plan_json(op, chi, chi, m.PREC_BF16X3)
+    made, skipped = set(), 0
+    for dg in plan["diagrams"]:
+        for st in dg["steps"]:
+            if st["kind"] != "permute":
+                continue
+            key = (st["slot"], st["rows"], st["cols"], st["ld"], str(st["row_src"]), str(st["col_src"]))
+            if st["skip"]:
+                assert key in made
+                skipped += 1
+            else:
+                assert key not in made or not dg["bufs"][st["dst_buf"]]["resident"]
+                made.add(key)
+    assert skipped > 0
+    if op == m.OP_DESCEND:  # both diagrams read rho in the same layout
+        rho_copies = [st for dg in plan["diagrams"] for st in dg["steps"]
+                      if st["kind"] == "permute" and st["slot"] == 1 and not st["skip"]]
+        assert len(rho_copies) == 1

@@ -128,8 +128,9 @@ struct Arena {
 };
 
 // Execute a contraction program; inputs[slot] are device pointers.
-// reuse_resident: the u/w operand copies (resident == 1) left by the previous run of this
-// same program (same u, w, workspace) are still valid; skip those copies.
+// reuse_resident: the u/w operand copies (resident == 1) and the u/w-only
+// products left by the previous run of this same program (same u, w,
+// workspace) are still valid; skip those steps.
 mera_status run_program(const OpProgram& prog, const double* const inputs[4], double* out, int prec, char* ws,
                         cudaStream_t stream, bool reuse_resident = false) {
   for (const Program& dg : prog.diagrams) {
@@ -145,6 +146,7 @@ mera_status run_program(const OpProgram& prog, const double* const inputs[4], do
         continue;
       }
       const GemmStep& g = st.g;
+      if (reuse_resident && g.stat) continue;  // u/w-only product kept from the previous run
       const Buffer& a = dg.bufs[g.a_buf];
       const Buffer& b = dg.bufs[g.b_buf];
       ProfScope ps(stream, 0, g.dominant, g.flops);
@@ -394,6 +396,8 @@ extern "C" mera_status mera_polar_update(const double* env, int m, int n, double
     g.M = n; g.N = n; g.K = m;
     g.C = G; g.m_dst = row_n; g.n_dst = col_1; g.alpha = 1.0; g.accumulate = 0;
     if ((e = launch_gemm_f64(g, s)) != cudaSuccess) return cuda_status(e, "polar gemm 1");
+    if (it == 0 && (e = launch_ns_prescale(G, src, m, n, scalars + 2, s)) != cudaSuccess)
+      return cuda_status(e, "polar prescale");
     if ((e = launch_ns_step(G, Bm, n, red, scalars + 1, tol, state, s)) != cudaSuccess)
       return cuda_status(e, "polar step");
     // X_next = X (3 I - X^T X) / 2

@@ -47,6 +47,9 @@ cudaError_t launch_sym_normalize(const double* X, double* rho, int64_t n, double
                                  double* scalars, double* resid, cudaStream_t stream);
 
 // Polar-iteration helpers (all binary64, deterministic reductions).
+// G = X^T X (n x n) and X (m x n) scaled by 1/c and 1/sqrt(c), c = max row
+// abs sum of G (>= its largest eigenvalue), written to *c.
+cudaError_t launch_ns_prescale(double* G, double* X, int64_t m, int64_t n, double* c, cudaStream_t stream);
 cudaError_t launch_frob_scale(const double* src, double* dst, int64_t count, double* partials,
                               double* scalars, cudaStream_t stream);
 // One gated Newton-Schulz step's elementwise part: Bm = (3I - G)/2, resid =

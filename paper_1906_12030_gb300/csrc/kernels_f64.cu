@@ -523,6 +523,51 @@ __global__ void __launch_bounds__(256) scale_by_inverse_kernel(const double* __r
     dst[i] = src[i] * s;
 }
 
+// Gershgorin rescale of the first Newton-Schulz step: with G = X^T X and
+// c = max_i sum_j |G_ij| >= lambda_max(G), X / sqrt(c) has every singular
+// value in (0, 1] and the same polar factor, usually much closer to 1 than
+// the Frobenius scaling leaves them.
+__global__ void __launch_bounds__(1024) ns_gershgorin_kernel(const double* __restrict__ G, int64_t n, double* c) {
+  __shared__ double sm[32];
+  double v = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double r = 0.0;
+    for (int64_t j = 0; j < n; ++j) r += fabs(G[i * n + j]);
+    v = fmax(v, r);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) *c = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) ns_prescale_kernel(double* G, int64_t gcount, double* X, int64_t xcount,
+                                                          const double* __restrict__ c) {
+  const double ig = 1.0 / *c, ix = 1.0 / sqrt(*c);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < gcount + xcount;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    if (i < gcount)
+      G[i] *= ig;
+    else
+      X[i - gcount] *= ix;
+  }
+}
+
+cudaError_t launch_ns_prescale(double* G, double* X, int64_t m, int64_t n, double* c, cudaStream_t stream) {
+  count_launch(2);
+  ns_gershgorin_kernel<<<1, 1024, 0, stream>>>(G, n, c);
+  const int64_t total = n * n + m * n;
+  const int nb = int(std::min<int64_t>((total + 255) / 256, 1024));
+  ns_prescale_kernel<<<nb, 256, 0, stream>>>(G, n * n, X, m * n, c);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_frob_scale(const double* src, double* dst, int64_t count, double* partials, double* scalars,
                               cudaStream_t stream) {
   const int nb = int(std::min<int64_t>((count + 255) / 256, 1024));

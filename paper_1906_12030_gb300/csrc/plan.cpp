@@ -251,6 +251,7 @@ struct Builder {
   // slice_block[P2] = b: each slice covers b consecutive values of the leg.
   std::vector<int> slice_leg, sliced_child;
   std::vector<int64_t> slice_block;
+  std::vector<char> is_static;  // the node's value depends on u and w only
   std::vector<char> deferred;
   size_t slice_threshold = 0;
   // Copies of h or rho that several diagrams of the operation read in the
@@ -322,6 +323,10 @@ struct Builder {
     gs.lda = prog.bufs[gs.a_buf].ld;
     gs.ldb = prog.bufs[gs.b_buf].ld;
     gs.c_buf = (i == tr.root) ? -1 : buf_of[i];
+    if (i != tr.root && is_static[i]) {
+      gs.stat = 1;
+      prog.bufs[buf_of[i]].resident = 1;
+    }
     gs.c_ld = (i == tr.root) ? 0 : prog.bufs[buf_of[i]].ld;
     const bool is_producer = (l >= 0) && deferred[i];  // writes the one-slice buffer
     if (l >= 0) {
@@ -392,6 +397,16 @@ struct Builder {
     tr = plan_order(tmask, dim, 7);
     if (tr.root < 0) return false;
     const size_t nn = tr.nodes.size();
+    is_static.assign(nn, 0);
+    for (size_t i = 0; i < nn; ++i) {  // children precede their parent in the node list
+      const Node& nd = tr.nodes[i];
+      if (nd.tensor >= 0) {
+        const int slot = dg.tensors[nd.tensor].slot;
+        is_static[i] = (slot == SLOT_U || slot == SLOT_W);
+      } else {
+        is_static[i] = is_static[nd.left] && is_static[nd.right];
+      }
+    }
     dst_stride.assign(nn, {});
     buf_of.assign(nn, -1);
     g.assign(nn, {});
@@ -695,16 +710,19 @@ const OpProgram* get_program(int op, int chi_b, int chi_t, int prec) {
       if (!prog) return nullptr;
     }
   }
-  // Workspace: [resident copies, one per distinct copy][transient arena].
-  // A later step making a copy that already exists is skipped.
+  // Workspace: [resident buffers][transient arena].  Resident buffers are
+  // input copies (one per distinct copy: a later step making a copy that
+  // already exists is skipped) and the outputs of u/w-only GEMM steps.
   size_t res_base = 0;
   {
     std::map<std::string, int64_t> made;  // key -> offset
-    for (Program& pg : prog->diagrams)
+    for (Program& pg : prog->diagrams) {
+      std::vector<char> placed(pg.bufs.size(), 0);
       for (Step& st : pg.steps) {
         if (st.kind != 0) continue;
         Buffer& bf = pg.bufs[st.p.dst_buf];
         if (!bf.resident) continue;
+        placed[size_t(st.p.dst_buf)] = 1;
         const std::string k = permute_key(st.p);
         auto it = made.find(k);
         if (it != made.end()) {
@@ -716,6 +734,12 @@ const OpProgram* get_program(int op, int chi_b, int chi_t, int prec) {
           res_base += size_t(bf.bytes + 255) / 256 * 256;
         }
       }
+      for (size_t b = 0; b < pg.bufs.size(); ++b)
+        if (pg.bufs[b].resident && !placed[b]) {
+          pg.bufs[b].offset = int64_t(res_base);
+          res_base += size_t(pg.bufs[b].bytes + 255) / 256 * 256;
+        }
+    }
   }
   prog->persistent_bytes = res_base;
   size_t trans = 0;
@@ -780,7 +804,7 @@ std::string program_json(const OpProgram& prog, int op, int chi_b, int chi_t, in
           << ",\"c_buf\":" << g.c_buf << ",\"alpha\":" << g.alpha << ",\"accumulate\":" << g.accumulate
           << ",\"flops\":" << g.flops << ",\"dominant\":" << g.dominant << ",\"split\":" << g.split
           << ",\"p_buf\":" << g.p_buf << ",\"a_off\":" << g.a_off << ",\"b_off\":" << g.b_off
-          << ",\"c_off\":" << g.c_off << ",\"m_dst\":";
+          << ",\"c_off\":" << g.c_off << ",\"stat\":" << g.stat << ",\"m_dst\":";
         lm(g.m_dst);
         o << ",\"n_dst\":";
         lm(g.n_dst);

@@ -56,6 +56,8 @@ struct GemmStep {
   int split = 1;      // K split over this many CTAs (tensor-core modes; partials summed in FP64)
   int64_t a_off = 0, b_off = 0, c_off = 0;  // element offsets into A, B and the destination (slices)
   int p_buf = -1;     // FP32 partial-sum buffer [split][N][M] when split > 1
+  int stat = 0;       // reads only u and w (directly or through such steps): its output is kept
+                      // for the call, and a later run with the same u, w may skip the step
   std::string label;  // e.g. "aceiq*CDcdil->ADadelq" for inspection
 };
 

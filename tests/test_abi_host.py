@@ -98,11 +98,15 @@ def _offsets(lm, count):
     return off
 
 
-def _emulate(plan, inputs, out_size):
-    """Run a program in float64; buffers live in one flat arena (per plane)."""
+def _emulate(plan, inputs, out_size, arena=None, reuse=False, keep=False):
+    """Run a program in float64; buffers live in one flat arena (per plane).
+    reuse: run it again on the arena of a previous run with the same u and w,
+    skipping the u/w copies and the u/w-only products as the library does.
+    keep: return (output, arena)."""
     eb = plan["elem_bytes"]
     out = np.zeros(out_size)
-    arena = np.full(plan["ws_bytes"] // eb + 1, np.nan)
+    if arena is None:
+        arena = np.full(plan["ws_bytes"] // eb + 1, np.nan)
     for dg in plan["diagrams"]:
         bufs = dg["bufs"]
         partial = {st["p_buf"] for st in dg["steps"] if st["kind"] == "gemm" and st["p_buf"] >= 0}
@@ -121,6 +125,11 @@ def _emulate(plan, inputs, out_size):
                 b = bufs[st["dst_buf"]]
                 assert b["resident"] and b["offset"] + b["bytes"] <= plan["persistent_bytes"]
                 continue  # the same copy was made by an earlier step
+            if reuse and st["kind"] == "permute" and bufs[st["dst_buf"]]["resident"] == 1:
+                continue  # u/w copy kept from the previous run
+            if reuse and st["kind"] == "gemm" and st["stat"]:
+                assert bufs[st["c_buf"]]["resident"] == 1
+                continue  # u/w-only product kept from the previous run
             if st["kind"] == "permute":
                 src = inputs[st["slot"]].reshape(-1)
                 b = bufs[st["dst_buf"]]
@@ -158,7 +167,7 @@ def _emulate(plan, inputs, out_size):
                     assert idx.min() >= 0 and idx.max() < cb["rows"] * cb["ld"]
                     assert (idx % cb["ld"]).max() < bufs[st["c_buf"]]["ld"]
                     arena[cb["offset"] // eb + idx] = C
-    return out
+    return (out, arena) if keep else out
 
 
 _SMALL = [(2, 2), (3, 3), (2, 3), (4, 3), (3, 5)]
@@ -314,3 +323,27 @@ def test_identical_input_copies_are_made_once(op, chi):
         rho_copies = [st for dg in plan["diagrams"] for st in dg["steps"]
                       if st["kind"] == "permute" and st["slot"] == 1 and not st["skip"]]
         assert len(rho_copies) == 1
+
+
+@pytest.mark.parametrize("prec,chi", [(m.PREC_F64, 3), (m.PREC_BF16X3, 4)])
+def test_rerun_with_kept_uw_products(prec, chi):
+    """The power iteration runs the descending program again with new rho and
+    the same u, w, skipping the u/w copies and the u/w-only products it kept:
+    the second run must still give the oracle's D(rho2), and every kept
+    product must read only kept buffers."""
+    rng = np.random.default_rng(31)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    r1, r2 = I.random_density(rng, chi), I.random_density(rng, chi)
+    plan = m.mera_plan_json(m.OP_DESCEND, chi, chi, prec)
+    n_stat = 0
+    for dg in plan["diagrams"]:
+        for st in dg["steps"]:
+            if st["kind"] == "gemm" and st["stat"]:
+                n_stat += 1
+                assert dg["bufs"][st["a_buf"]]["resident"] == 1 and dg["bufs"][st["b_buf"]]["resident"] == 1
+    assert n_stat == 8  # four u/w products in each of the two diagrams
+    out1, arena = _emulate(plan, [None, r1, u, w], chi ** 6, keep=True)
+    out2 = _emulate(plan, [None, r2, u, w], chi ** 6, arena=arena, reuse=True)
+    for got, rho in ((out1, r1), (out2, r2)):
+        want = O.descend(rho, u, w).reshape(-1)
+        assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max())

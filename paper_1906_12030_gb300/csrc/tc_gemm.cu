@@ -21,6 +21,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "../../include/mera.h"
@@ -181,7 +182,29 @@ struct Epilogue {
   int kc;           // k-blocks per split
   float* partial;   // split > 1: raw FP32 partials [split][N][M], summed by splitk_reduce_kernel
   int off32;        // every column offset n_dst(n) is below 2^31
+  int alpha_exp;    // alpha == 2^alpha_exp exactly (alpha_pow2 set)
+  int alpha_pow2;
 };
+
+// binary32 -> binary64 times 2^e by integer operations, exact.  The FP64 pipe
+// of this GPU runs at a small fraction of its FP32 rate, so a conversion and
+// a multiply per element in FP64 made the caller-format epilogue several
+// times slower than its stores.  Zero, subnormal, infinite and NaN inputs
+// take the arithmetic path (rare).
+__device__ __forceinline__ double f32_to_f64_pow2(float f, int e) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t ex = (u >> 23) & 0xFFu, mant = u & 0x7FFFFFu;
+  uint64_t bits = uint64_t(u & 0x80000000u) << 32;  // sign; zero stays a signed zero
+  if (ex == 0xFFu) {
+    bits |= (uint64_t(0x7FFu) << 52) | (uint64_t(mant) << 29);  // infinity, NaN
+  } else if (ex != 0u) {  // normal: rebias the exponent, widen the fraction
+    bits |= (uint64_t(ex + (1023u - 127u) + uint32_t(e)) << 52) | (uint64_t(mant) << 29);
+  } else if (mant != 0u) {  // subnormal: mant * 2^-149 = 2^(p - 149) * (mant / 2^p), p = msb of mant
+    const int p = 31 - __clz(mant);
+    bits |= (uint64_t(p - 149 + 1023 + e) << 52) | ((uint64_t(mant) - (uint64_t(1) << p)) << (52 - p));
+  }
+  return __longlong_as_double(static_cast<long long>(bits));
+}
 
 // Stages hold 128-byte slabs (64 BF16 or 32 TF32 along K) of every plane.
 // (64-byte slabs, which fit twice as many stages for the split-BF16 modes,
@@ -222,9 +245,9 @@ __device__ __forceinline__ void store_chunk(void* C, int64_t off_m, int64_t c_pl
       r[q.w] = round_tf32(__uint_as_float(v[j + 3]));
     }
   } else {
-    __nv_bfloat16* r0 = static_cast<__nv_bfloat16*>(C) + off_m;
-    __nv_bfloat16* r1 = r0 + c_plane;
-    __nv_bfloat16* r2 = r1 + c_plane;
+    __nv_bfloat16* __restrict__ r0 = static_cast<__nv_bfloat16*>(C) + off_m;
+    __nv_bfloat16* __restrict__ r1 = r0 + c_plane;
+    __nv_bfloat16* __restrict__ r2 = r1 + c_plane;
 #pragma unroll
     for (int j = 0; j < 32; j += 2) {
       const int2 q = *reinterpret_cast<const int2*>(s_off + j);
@@ -383,6 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ch_lo = (sub * kChunks) / kSub, ch_hi = ((sub + 1) * kChunks) / kSub;
     const float alpha = float(ep.alpha);
     const bool fast_ok = !ep.c_final && ep.split <= 1 && ep.off32 && ep.alpha == 1.0;
+    const bool final_fast = ep.c_final && ep.split <= 1 && ep.off32 && ep.alpha_pow2;
     uint32_t tc = 0;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++tc) {
       const int64_t mn = t % tiles_mn, ks = t / tiles_mn;
@@ -434,6 +458,31 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (fast_ok && c0 + 32 <= BN && n0 + c0 + 32 <= ep.N) {
           // whole chunk, operand-format destination, offsets in 32 bits
           store_chunk<PREC>(ep.C, off_m, ep.c_plane, off_n32 + c0, v);
+          continue;
+        }
+        if (final_fast && c0 + 32 <= BN && n0 + c0 + 32 <= ep.N) {
+          // whole chunk into the caller's binary64 output, alpha a power of two
+          double* __restrict__ r = static_cast<double*>(ep.C) + off_m;
+          const int* __restrict__ so = off_n32 + c0;
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {
+            // four offsets in registers before the four stores
+            const int4 q4 = *reinterpret_cast<const int4*>(so + j);
+            const int o[4] = {q4.x, q4.y, q4.z, q4.w};
+            double x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = f32_to_f64_pow2(__uint_as_float(v[j + q]), ep.alpha_exp);
+            if (ep.accumulate) {
+              double y[4];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) y[q] = r[o[q]];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) r[o[q]] = y[q] + x[q];
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) r[o[q]] = x[q];
+            }
+          }
           continue;
         }
 #pragma unroll
@@ -566,6 +615,12 @@ cudaError_t launch_cfg(const TcGemmArgs& a, cudaStream_t stream) {
   ep.m_dst = a.m_dst;
   ep.n_dst = a.n_dst;
   ep.alpha = a.alpha;
+  {
+    int e2 = 0;
+    const double fr = std::frexp(a.alpha, &e2);  // alpha = fr * 2^e2, fr in [0.5, 1)
+    ep.alpha_pow2 = (fr == 0.5) ? 1 : 0;
+    ep.alpha_exp = e2 - 1;
+  }
   ep.accumulate = a.accumulate;
   ep.c_final = a.c_final ? 1 : 0;
   const int64_t num_k = (a.K + C::kBK - 1) / C::kBK;

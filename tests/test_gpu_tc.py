@@ -69,6 +69,23 @@ def test_gemm_bound(prec, M, N, K):
     assert np.all(np.abs(got - exact) <= bound), float(np.max(np.abs(got - exact) / bound))
 
 
+@pytest.mark.parametrize("prec", TC_PRECS)
+@pytest.mark.parametrize("M,N,K", [(256, 256, 64), (300, 70, 40)])
+def test_gemm_exact_on_small_integers(prec, M, N, K):
+    """Small-integer operands are exact in every operand format and their
+    products and sums (|c| <= 64 * K) are exact in the FP32 accumulator, so
+    the caller's binary64 output must equal A B^T bit for bit: this pins the
+    epilogue's binary32 -> binary64 conversion, including signs and zeros."""
+    rng = np.random.default_rng(M + N + K)
+    A = rng.integers(-8, 9, size=(M, K)).astype(np.float64)
+    B = rng.integers(-8, 9, size=(N, K)).astype(np.float64)
+    A[0, :] = 0.0  # a zero row: signed zeros in the output
+    C = torch.empty(M * N, dtype=torch.float64, device="cuda")
+    m.mera_gemm_test(prec, _cuda(A), _cuda(B), C)
+    got = C.cpu().numpy().reshape(M, N)
+    assert np.array_equal(got, A @ B.T)
+
+
 def _maps(prec, chi_b, chi_t, seed):
     rng = np.random.default_rng(seed)
     u, w = I.random_u(rng, chi_b), I.random_w(rng, chi_b, chi_t)

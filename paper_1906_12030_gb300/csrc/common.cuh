@@ -54,6 +54,9 @@ struct OperandStore<PREC_F64> {
   __device__ __forceinline__ static void store(void* base, int64_t off, int64_t, double v) {
     static_cast<double*>(base)[off] = v;
   }
+  __device__ __forceinline__ static void store_f(void* base, int64_t off, int64_t, float f) {
+    static_cast<double*>(base)[off] = double(f);
+  }
 };
 // The reduced-precision stores convert binary64 -> binary32 once and split in
 // FP32: GB300's FP64 pipe is ~1/1800 of its BF16 tensor rate, so every extra
@@ -63,21 +66,29 @@ template <>
 struct OperandStore<PREC_TF32> {
   using T = float;
   __device__ __forceinline__ static void store(void* base, int64_t off, int64_t, double v) {
-    static_cast<float*>(base)[off] = round_tf32(__double2float_rn(v));
+    store_f(base, off, 0, __double2float_rn(v));
+  }
+  __device__ __forceinline__ static void store_f(void* base, int64_t off, int64_t, float f) {
+    static_cast<float*>(base)[off] = round_tf32(f);
   }
 };
 template <>
 struct OperandStore<PREC_BF16> {
   using T = __nv_bfloat16;
   __device__ __forceinline__ static void store(void* base, int64_t off, int64_t, double v) {
-    static_cast<__nv_bfloat16*>(base)[off] = __float2bfloat16_rn(__double2float_rn(v));
+    store_f(base, off, 0, __double2float_rn(v));
+  }
+  __device__ __forceinline__ static void store_f(void* base, int64_t off, int64_t, float f) {
+    static_cast<__nv_bfloat16*>(base)[off] = __float2bfloat16_rn(f);
   }
 };
 template <>
 struct OperandStore<PREC_BF16X3> {
   using T = __nv_bfloat16;
   __device__ __forceinline__ static void store(void* base, int64_t off, int64_t plane, double v) {
-    const float f = __double2float_rn(v);
+    store_f(base, off, plane, __double2float_rn(v));
+  }
+  __device__ __forceinline__ static void store_f(void* base, int64_t off, int64_t plane, float f) {
     const __nv_bfloat16 hi = __float2bfloat16_rn(f);
     const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
     static_cast<__nv_bfloat16*>(base)[off] = hi;
@@ -88,7 +99,9 @@ template <>
 struct OperandStore<PREC_BF16X6> {
   using T = __nv_bfloat16;
   __device__ __forceinline__ static void store(void* base, int64_t off, int64_t plane, double v) {
-    const float f = __double2float_rn(v);
+    store_f(base, off, plane, __double2float_rn(v));
+  }
+  __device__ __forceinline__ static void store_f(void* base, int64_t off, int64_t plane, float f) {
     const __nv_bfloat16 hi = __float2bfloat16_rn(f);
     const float r1 = f - __bfloat162float(hi);
     const __nv_bfloat16 mid = __float2bfloat16_rn(r1);

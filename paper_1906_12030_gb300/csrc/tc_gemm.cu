@@ -186,11 +186,11 @@ struct Epilogue {
   int alpha_pow2;
 };
 
-// binary32 -> binary64 times 2^e by integer operations, exact.  The FP64 pipe
-// of this GPU runs at a small fraction of its FP32 rate, so a conversion and
-// a multiply per element in FP64 made the caller-format epilogue several
-// times slower than its stores.  Zero, subnormal, infinite and NaN inputs
-// take the arithmetic path (rare).
+// binary32 -> binary64 times 2^e by integer operations, exact for every
+// class of input (zero, subnormal, normal, infinity, NaN; e must keep a
+// normal result in range).  The FP64 pipe of this GPU runs at a small
+// fraction of its FP32 rate, so a conversion and a multiply per element in
+// FP64 made the caller-format epilogue several times slower than its stores.
 __device__ __forceinline__ double f32_to_f64_pow2(float f, int e) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t ex = (u >> 23) & 0xFFu, mant = u & 0x7FFFFFu;
@@ -529,9 +529,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// Sum of the K-split partials in binary64 (fixed order), then the same
-// epilogue as the GEMM: alpha, conversion and scattered store.  One thread per
-// row m, looping over a chunk of columns.
+// Sum of the K-split partials in a fixed order, then the same epilogue as
+// the GEMM.  The sum is kept as an unevaluated pair hi + lo of binary32
+// values (Knuth's TwoSum per partial), which carries ~48 significant bits
+// like a binary64 sum but runs on the FP32 pipe.  One thread per row m,
+// looping over a chunk of columns.
 template <int PREC>
 __global__ void __launch_bounds__(256) splitk_reduce_kernel(const __grid_constant__ Epilogue ep) {
   const int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -540,15 +542,22 @@ __global__ void __launch_bounds__(256) splitk_reduce_kernel(const __grid_constan
   const int64_t n_per = (ep.N + gridDim.y - 1) / gridDim.y;
   const int64_t n_lo = int64_t(blockIdx.y) * n_per, n_hi = min(ep.N, n_lo + n_per);
   for (int64_t n = n_lo; n < n_hi; ++n) {
-    double acc = 0.0;
-    for (int s = 0; s < ep.split; ++s) acc += double(ep.partial[(int64_t(s) * ep.N + n) * ep.M + m]);
-    const double val = ep.alpha * acc;
+    float hi = 0.0f, lo = 0.0f;
+    for (int s = 0; s < ep.split; ++s) {
+      const float x = ep.partial[(int64_t(s) * ep.N + n) * ep.M + m];
+      const float t = __fadd_rn(hi, x);
+      const float xp = __fsub_rn(t, hi);
+      lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, xp)), __fsub_rn(x, xp)));
+      hi = t;
+    }
     const int64_t off = off_m + legmap_offset32(ep.n_dst, uint32_t(n));
     if (ep.c_final) {
       double* dst = static_cast<double*>(ep.C) + off;
+      const double val = ep.alpha_pow2 ? f32_to_f64_pow2(hi, ep.alpha_exp) + f32_to_f64_pow2(lo, ep.alpha_exp)
+                                       : ep.alpha * (double(hi) + double(lo));
       *dst = ep.accumulate ? (*dst + val) : val;
     } else {
-      OperandStore<PREC>::store(ep.C, off, ep.c_plane, val);
+      OperandStore<PREC>::store_f(ep.C, off, ep.c_plane, __fmul_rn(float(ep.alpha), __fadd_rn(hi, lo)));
     }
   }
 }

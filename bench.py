@@ -53,6 +53,7 @@ def _args():
                     help="slice rank-7 intermediates larger than this many GiB (library default 16)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="skip the replayed-graph timing of the sweep")
     ap.add_argument("--sweeps", type=int, default=300, help="--case precision: optimisation sweeps per run")
     ap.add_argument("--polish", type=int, default=20, help="--case precision: FP64 sweeps after the mixed ones")
     ap.add_argument("--scaling-k", type=int, default=0,
@@ -277,6 +278,15 @@ def run_native(args):
     torch.cuda.synchronize(dev)
 
     sweep_flops = _sweep_flops(m, chi)
+
+    def max_over_ranks(x):
+        if world > 1:
+            t = torch.tensor([x], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            return t.item()
+        return x
+
+    # ---- direct calls (mera_sweep per step), with per-kernel timing -------
     launches0 = m.mera_launch_count()
     m.mera_profile_enable(True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -284,7 +294,7 @@ def run_native(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
-    with ClockSampler(local) as clk:
+    with ClockSampler(local) as clk_direct:
         for k in range(args.steps):
             flush.fill_(k & 0xFF)  # evict L2 between timed steps (not timed)
             starts[k].record(stream)
@@ -293,24 +303,56 @@ def run_native(args):
         torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
-    launches = m.mera_launch_count() - launches0
-    step_ms = [s.elapsed_time(t) for s, t in zip(starts, ends)]
-    total_ms = sum(step_ms)
+    launches_direct = m.mera_launch_count() - launches0
+    direct_ms = max_over_ranks(sum(s_.elapsed_time(t_) for s_, t_ in zip(starts, ends)))
     dom = m.mera_profile_read(m.PROF_GEMM_DOMINANT)
     allg = m.mera_profile_read(m.PROF_GEMM)
     perm = m.mera_profile_read(m.PROF_PERMUTE)
     m.mera_profile_enable(False)
     energy = e.item()
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = t.item()
+    direct = {"value": world * args.steps / (direct_ms / 1e3), "unit": "sweep/s",
+              "ms_per_step": direct_ms / args.steps, "gpu_launches": launches_direct, "clocks": clk_direct.summary(),
+              "note": "one mera_sweep call per step; per-kernel CUDA events for the roofline and stage split"}
+
+    # ---- the same sweep recorded once as a CUDA graph and replayed ---------
+    # (mera_sweep_graph_create / mera_graph_launch: the public path for
+    # repeated sweeps; every replay performs the whole sweep)
+    graph_ms, launches, clk, gr, gdev = None, launches_direct, clk_direct, None, None
+    if not args.no_graph:
+        gus, gws, grho, ge, _ = make_state(prec)
+        gstate = m.MeraState(gus, gws, grho)
+        gwsb = m.workspace(m.mera_sweep_workspace_size(gstate.chi_b, gstate.chi_t, prec), dev)
+        gr = m.mera_sweep_graph(gstate, h1, shift, N_POW, ge, prec=prec, ws=gwsb, stream=stream)
+        gdev = gus + gws + [grho, h1]
+        for _ in range(args.warmup):
+            gr.launch(stream)
+        torch.cuda.synchronize(dev)
+        gs_ = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ge_ = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        launches0 = m.mera_launch_count()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        with ClockSampler(local) as clk:
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)
+                gs_[k].record(stream)
+                gr.launch(stream)
+                ge_[k].record(stream)
+            torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        launches = m.mera_launch_count() - launches0
+        graph_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(gs_, ge_)))
+        energy = ge.item()
+    total_ms = graph_ms if graph_ms is not None else direct_ms
 
     # ---- end to end through the C ABI with host buffers -------------------
     e2e = None
     if not args.no_e2e:
-        host = [t.detach().cpu().pin_memory() for t in us + ws_ + [rho, h1]]
-        devs = us + ws_ + [rho, h1]
+        devs = gdev if gr is not None else us + ws_ + [rho, h1]
+        eout = ge if gr is not None else e
+        host = [t.detach().cpu().pin_memory() for t in devs]
         e_host = torch.empty(1, dtype=torch.float64).pin_memory()
         h2d = sum(t.numel() * t.element_size() for t in host)
         n_e2e = max(1, min(args.steps, 2))
@@ -321,17 +363,19 @@ def run_native(args):
         for _ in range(n_e2e):
             for hsrc, ddst in zip(host, devs):
                 ddst.copy_(hsrc, non_blocking=True)
-            sweep()
-            e_host.copy_(e, non_blocking=True)
+            if gr is not None:
+                gr.launch(stream)
+            else:
+                sweep()
+            e_host.copy_(eout, non_blocking=True)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
-        e2e_ms = ev0.elapsed_time(ev1)
-        if world > 1:
-            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = t.item()
+        e2e_ms = max_over_ranks(ev0.elapsed_time(ev1))
         e2e = {"value": world * n_e2e / (e2e_ms / 1e3), "unit": "sweep/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": 8, "steps": n_e2e}
+               "d2h_bytes_per_step": 8, "steps": n_e2e,
+               "path": "graph replay" if gr is not None else "mera_sweep"}
+    if gr is not None:
+        gr.close()
 
     # ---- the same MERA with FP64 contractions: throughput and energy gap ----
     fp64 = None
@@ -369,7 +413,9 @@ def run_native(args):
                                f"{N_POW} rho* power steps, blocked d=4", "chi": chi, "n_pow": N_POW, "hz": HZ,
                    "prec": args.prec, "seed": SEED, "layer_dims": I.layer_dims(chi),
                    "sweep_flops": sweep_flops, "parallelism": f"replicas{world}",
-                   "l2": "256 MB buffer written between timed steps (untimed); working set > L2"},
+                   "l2": "256 MB buffer written between timed steps (untimed); working set > L2",
+                   "launch": "mera_sweep recorded once as a CUDA graph, replayed each step" if graph_ms is not None
+                   else "one mera_sweep call per step"},
         "energy_per_spin": energy,
         "fp64": fp64,
         "roofline": {"bound": "tensor" if args.prec != "f64" else "fp64", "achieved": dom_tflops, "peak": peak,
@@ -381,6 +427,7 @@ def run_native(args):
         "stage_ms_per_step": {"gemm": allg[1] / args.steps, "gemm_dominant": dom[1] / args.steps,
                               "permute": perm[1] / args.steps},
         "gpu_launches": launches,
+        "direct": direct,
         "clocks": clk.summary(),
         "e2e": e2e,
     }
@@ -486,13 +533,25 @@ def run_batch(args):
 
     flops = sum(_sweep_flops(m, chi) for _, chi, _ in specs)
     res = {}
-    for mode in ("one_at_a_time", "batched"):
+    for mode in ("one_at_a_time", "batched", "graphs"):
         ms = make()
         e = torch.empty(len(ms), dtype=torch.float64, device="cuda")
         streams = [torch.cuda.Stream() for _ in ms]
+        graphs = []
+        if mode == "graphs":  # one recorded sweep per MERA, replayed on its own stream
+            for i, (st, h1, shift, wsb) in enumerate(ms):
+                graphs.append(m.mera_sweep_graph(st, h1, shift, N_POW, e[i:i + 1], prec=prec, ws=wsb,
+                                                 stream=streams[i]))
 
         def step():
-            if mode == "batched":
+            if mode == "graphs":
+                cur = torch.cuda.current_stream()
+                for g, sm in zip(graphs, streams):
+                    sm.wait_stream(cur)
+                    g.launch(sm)
+                for sm in streams:
+                    cur.wait_stream(sm)
+            elif mode == "batched":
                 try:
                     m.mera_sweep_batch([x[0] for x in ms], [x[1] for x in ms], [x[2] for x in ms], N_POW, e,
                                        prec=prec, wss=[x[3] for x in ms], streams=streams, n_threads=16)
@@ -515,14 +574,19 @@ def run_batch(args):
         dt = (time.perf_counter() - t0) / args.steps
         res[mode] = {"mera_sweeps_per_s": len(ms) / dt, "ms_per_step": dt * 1e3, "tflops": flops / dt / 1e12,
                      "energies": e.cpu().tolist()}
+        for g in graphs:
+            g.close()
         del ms
-    same = res["batched"]["energies"] == res["one_at_a_time"]["energies"]
+    same = (res["batched"]["energies"] == res["one_at_a_time"]["energies"]
+            and res["graphs"]["energies"] == res["one_at_a_time"]["energies"])
     for r in res.values():
         r.pop("energies")
+    base = res["one_at_a_time"]["mera_sweeps_per_s"]
     print(json.dumps({"case": "batch", "prec": args.prec, "n_meras": len(specs),
                       "chis": [c for _, c, _ in specs], "steps": args.steps, "warmup": args.warmup,
-                      "results": res, "speedup": res["batched"]["mera_sweeps_per_s"] /
-                      res["one_at_a_time"]["mera_sweeps_per_s"], "identical_energies": same}), flush=True)
+                      "results": res, "speedup": res["batched"]["mera_sweeps_per_s"] / base,
+                      "speedup_graphs": res["graphs"]["mera_sweeps_per_s"] / base,
+                      "identical_energies": same}), flush=True)
 
 
 def run_precision(args):

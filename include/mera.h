@@ -253,10 +253,36 @@ mera_status mera_flops(int op, int chi_b, int chi_t, double* flops);
 /*
  * Device-side failure word of the current device: bit (1 << MERA_ETIMEOUT)
  * is set when a bounded wait inside a tensor-core kernel gave up (the kernel
- * then skipped its remaining work and returned; its outputs are invalid).
+ * then skipped its remaining work and returned; its outputs are invalid);
+ * bit (1 << MERA_ENOTCONV) when a polar update recorded in a graph (below)
+ * did not converge within its recorded steps.
  * Synchronises with the device.  clear != 0 resets the word afterwards.
  */
 mera_status mera_device_status(int* status, int clear);
+
+/*
+ * One sweep recorded as a CUDA graph and replayed (Sec. II C; no
+ * counterpart in the paper's TensorFlow implementation).  Launching ~1200
+ * kernels per sweep from the host bounds small-chi sweeps and batches of
+ * MERAs; a replay issues them all with one call.
+ *
+ * mera_sweep_graph_create records mera_sweep(S, h1, shift, n_pow, prec, ws,
+ * ws_bytes, e_dev) issued on `stream` (which must not be the legacy
+ * default stream) into *graph; nothing is computed.  Every replay then
+ * performs that sweep on the same buffers: S's tensors, h1, ws and e_dev are
+ * captured by address and must stay allocated (and hold the state to update)
+ * until mera_graph_destroy.  Inside the recording every polar update runs
+ * 40 device-gated Newton-Schulz steps with no host check (steps after
+ * convergence return at once); non-convergence is reported through bit
+ * MERA_ENOTCONV of mera_device_status instead of a return status.  A replay
+ * gives bit-identical results to mera_sweep on the same inputs.
+ * mera_graph_launch enqueues one replay on `stream` (any stream).
+ */
+typedef struct mera_graph_s* mera_graph;
+mera_status mera_sweep_graph_create(mera_state* S, const double* h1, double shift, int n_pow, int prec, void* ws,
+                                    size_t ws_bytes, double* e_dev, void* stream, mera_graph* graph);
+mera_status mera_graph_launch(mera_graph graph, void* stream);
+mera_status mera_graph_destroy(mera_graph graph);
 
 /* ------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper; used to measure the kernels).

@@ -20,7 +20,7 @@ __all__ = [
     "mera_energy", "mera_ising_h1", "mera_sweep", "mera_sweep_workspace_size", "mera_plan_json", "mera_flops",
     "workspace", "MeraState", "mera_launch_count", "mera_profile_enable", "mera_profile_read",
     "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE", "mera_device_status", "mera_gemm_test",
-    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_sweep_batch", "mera_set_slice_bytes",
+    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_sweep_batch", "mera_set_slice_bytes", "MeraGraph", "mera_sweep_graph",
 ]
 
 PREC_F64, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3, 4
@@ -99,6 +99,9 @@ def library():
             "mera_ascend_noalloc": ([vp, vp, vp, i, i, vp, i, vp], i),
             "mera_op_transpose": ([vp, i, vp, vp], i),
             "mera_set_slice_bytes": ([sz], i),
+            "mera_sweep_graph_create": ([ctypes.POINTER(_State), vp, d, i, i, vp, sz, vp, vp, ctypes.POINTER(vp)], i),
+            "mera_graph_launch": ([vp, vp], i),
+            "mera_graph_destroy": ([vp], i),
             "mera_sweep_batch": ([ctypes.POINTER(_State), i, ctypes.POINTER(vp), ctypes.POINTER(d), i, i,
                                   ctypes.POINTER(vp), ctypes.POINTER(sz), vp, ctypes.POINTER(vp), i], i),
             "mera_profile_enable": ([i], i),
@@ -310,6 +313,47 @@ def mera_sweep(state: MeraState, h1, shift, n_pow, e_out, prec=PREC_F64, ws=None
     _check(library().mera_sweep(ctypes.byref(st), _f64(h1, state.chi_b[0] ** 6, "h1"), float(shift), n_pow, prec, p,
                                 n, _f64(e_out, 1, "e_out"), _stream(stream)))
     return e_out
+
+
+class MeraGraph:
+    """A sweep recorded as a CUDA graph (mera_sweep_graph_create).  Keeps the
+    recorded buffers alive; launch() replays the sweep on any stream."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        if self._h is None:
+            raise MeraError(1, "graph destroyed")
+        _check(library().mera_graph_launch(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h is not None:
+            library().mera_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mera_sweep_graph(state: MeraState, h1, shift, n_pow, e_out, prec=PREC_F64, ws=None, stream=None) -> MeraGraph:
+    """Record one mera_sweep into a CUDA graph (nothing is computed).  `stream`
+    must be a torch.cuda.Stream other than the legacy default stream."""
+    if stream is None:
+        raise MeraError(1, "graph capture needs a non-default stream")
+    if ws is None:
+        ws = workspace(mera_sweep_workspace_size(state.chi_b, state.chi_t, prec), h1.device)
+    p, n = _ws(ws)
+    st = state._c()
+    h = ctypes.c_void_p()
+    _check(library().mera_sweep_graph_create(ctypes.byref(st), _f64(h1, state.chi_b[0] ** 6, "h1"), float(shift),
+                                             n_pow, prec, p, n, _f64(e_out, 1, "e_out"), _stream(stream),
+                                             ctypes.byref(h)))
+    return MeraGraph(h, (state, h1, e_out, ws))
 
 
 def mera_launch_count() -> int:

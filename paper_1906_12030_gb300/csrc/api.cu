@@ -67,6 +67,11 @@ struct ProfScope {
     std::lock_guard<std::mutex> lk(g_prof.mu);
     on = g_prof.on;
     if (!on) return;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+      on = false;  // no per-step timing inside a captured graph
+      return;
+    }
     rec.a = g_prof.get();
     rec.b = g_prof.get();
     rec.kind = kind;
@@ -199,6 +204,11 @@ mera_status run_program(const OpProgram& prog, const double* const inputs[4], do
   }
   return MERA_OK;
 }
+
+// Newton-Schulz steps recorded for a polar update inside a stream capture
+// (the Gershgorin-scaled iteration converges in 10-15 steps on the sweep's
+// environments).
+constexpr int kCaptureNsSteps = 40;
 
 // Workspace bytes of each composite operation.
 size_t op_bytes(const OpProgram& p) { return align_up(p.ws_bytes); }
@@ -360,9 +370,16 @@ extern "C" mera_status mera_polar_update(const double* env, int m, int n, double
   const size_t need = polar_bytes(m, n);
   if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(MERA_EINVAL, "workspace not 256-byte aligned");
   if (!ws || ws_bytes < need) return fail(MERA_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
-  if (max_iter <= 0) max_iter = 100;
-  if (!(tol > 0)) tol = 1e-13 * std::sqrt(double(n));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // Inside a stream capture the host cannot look at the iteration state: a
+  // fixed number of device-gated steps is recorded instead (steps after
+  // convergence return at once) and non-convergence goes to the device
+  // status word.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return fail(MERA_ECUDA, "stream capture status");
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  if (max_iter <= 0) max_iter = capturing ? kCaptureNsSteps : 100;
+  if (!(tol > 0)) tol = 1e-13 * std::sqrt(double(n));
   Arena ar{static_cast<char*>(ws), ws_bytes};
   double* X = reinterpret_cast<double*>(ar.take(size_t(m) * n * sizeof(double)));
   double* Xn = reinterpret_cast<double*>(ar.take(size_t(m) * n * sizeof(double)));
@@ -407,7 +424,7 @@ extern "C" mera_status mera_polar_update(const double* env, int m, int n, double
     g.C = dst; g.m_dst = row_m; g.n_dst = col_1;
     if ((e = launch_gemm_f64(g, s)) != cudaSuccess) return cuda_status(e, "polar gemm 2");
     if ((e = launch_ns_finish(state, s)) != cudaSuccess) return cuda_status(e, "polar finish");
-    if ((it + 1) % kCheck == 0 || it + 1 == max_iter) {
+    if (!capturing && ((it + 1) % kCheck == 0 || it + 1 == max_iter)) {
       if ((e = cudaMemcpyAsync(host_state, state, sizeof host_state, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
           (e = cudaMemcpyAsync(&resid, scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_status(e, "polar state copy");
@@ -415,10 +432,13 @@ extern "C" mera_status mera_polar_update(const double* env, int m, int n, double
       if (host_state[0]) break;
     }
   }
-  const bool converged = host_state[0] && std::isfinite(resid) && resid <= tol;
-  X = buf[host_state[1] & 1];
-  e = launch_scale_copy(X, out, int64_t(m) * n, -1.0, s);
+  e = launch_ns_output(X, Xn, state, out, int64_t(m) * n, s);  // -X of the last step, chosen on the device
   if (e != cudaSuccess) return cuda_status(e, "polar output");
+  if (capturing) {
+    if ((e = launch_report_notconv(state, s)) != cudaSuccess) return cuda_status(e, "polar report");
+    return MERA_OK;
+  }
+  const bool converged = host_state[0] && std::isfinite(resid) && resid <= tol;
   if (!converged) return fail(MERA_ENOTCONV, "polar iteration did not converge (resid %.3e, tol %.3e)", resid, tol);
   return MERA_OK;
 }
@@ -559,10 +579,68 @@ extern "C" mera_status mera_sweep(mera_state* S, const double* h1, double shift,
   double* etmp = reinterpret_cast<double*>(base + L.etmp_off);
   st = mera_energy(h1, rho_above, S->u[0], S->w[0], S->chi_b[0], S->chi_t[0], etmp, prec, mws, mb, stream);
   if (st != MERA_OK) return st;
+  count_launch();
   energy_per_spin_kernel<<<1, 1, 0, s>>>(etmp, shift, e_dev);
   st = cuda_status(cudaGetLastError(), "energy per spin");
   if (st != MERA_OK) return st;
   if (notconv) return fail(MERA_ENOTCONV, "a polar update hit its iteration cap");
+  return MERA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// A sweep recorded once as a CUDA graph and replayed.
+// ---------------------------------------------------------------------------
+struct mera_graph_s {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;  // kernels in the graph
+};
+
+extern "C" mera_status mera_sweep_graph_create(mera_state* S, const double* h1, double shift, int n_pow, int prec,
+                                               void* ws, size_t ws_bytes, double* e_dev, void* stream,
+                                               mera_graph* out) {
+  if (!out) return fail(MERA_EINVAL, "null graph handle");
+  *out = nullptr;
+  if (!stream) return fail(MERA_EINVAL, "graph capture needs a stream other than the legacy default stream");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_status(e, "begin capture");
+  const long long l0 = g_launch_count.load();
+  const mera_status st = mera_sweep(S, h1, shift, n_pow, prec, ws, ws_bytes, e_dev, stream);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(s, &g);
+  if (st != MERA_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;  // message already recorded
+  }
+  if (e != cudaSuccess || !g) return cuda_status(e == cudaSuccess ? cudaErrorUnknown : e, "end capture");
+  cudaGraphExec_t x = nullptr;
+  if ((e = cudaGraphInstantiate(&x, g, 0)) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_status(e, "graph instantiate");
+  }
+  auto* h = new mera_graph_s;
+  h->graph = g;
+  h->exec = x;
+  h->launches = g_launch_count.load() - l0;
+  g_launch_count.fetch_sub(h->launches);  // counted when replayed
+  *out = h;
+  return MERA_OK;
+}
+
+extern "C" mera_status mera_graph_launch(mera_graph g, void* stream) {
+  if (!g || !g->exec) return fail(MERA_EINVAL, "null graph");
+  const cudaError_t e = cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_status(e, "graph launch");
+  count_launch(g->launches);
+  return MERA_OK;
+}
+
+extern "C" mera_status mera_graph_destroy(mera_graph g) {
+  if (!g) return MERA_OK;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
   return MERA_OK;
 }
 

@@ -58,6 +58,9 @@ cudaError_t launch_ns_step(const double* G, double* Bm, int64_t n, double* parti
                            int* state, cudaStream_t stream);
 // Closes a step: state[1] += 1; state[0] = state[2].  Skipped once state[0] is set.
 cudaError_t launch_ns_finish(int* state, cudaStream_t stream);
+// out = -(state[1] odd ? x1 : x0): the polar result, selected on the device.
+cudaError_t launch_ns_output(const double* x0, const double* x1, const int* state, double* out, int64_t count,
+                             cudaStream_t stream);
 cudaError_t launch_scale_copy(const double* src, double* dst, int64_t count, double alpha,
                               cudaStream_t stream);
 

@@ -637,6 +637,25 @@ __global__ void __launch_bounds__(256) scale_copy_kernel(const double* __restric
     dst[i] = alpha * src[i];
 }
 
+// out = -X with X the iterate the Newton-Schulz state points at (buffer
+// state[1] & 1), chosen on the device so that no host read is needed.  The
+// sign flip is a bit operation (exact, off the FP64 pipe).
+__global__ void __launch_bounds__(256) ns_output_kernel(const double* __restrict__ x0, const double* __restrict__ x1,
+                                                        const int* __restrict__ state, double* out, int64_t count) {
+  const double* src = (state[1] & 1) ? x1 : x0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = __longlong_as_double(__double_as_longlong(src[i]) ^ (1ll << 63));
+}
+
+cudaError_t launch_ns_output(const double* x0, const double* x1, const int* state, double* out, int64_t count,
+                             cudaStream_t stream) {
+  const int nb = int(std::min<int64_t>((count + 255) / 256, 1024));
+  if (nb <= 0) return cudaSuccess;
+  count_launch();
+  ns_output_kernel<<<nb, 256, 0, stream>>>(x0, x1, state, out, count);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scale_copy(const double* src, double* dst, int64_t count, double alpha, cudaStream_t stream) {
   const int nb = int(std::min<int64_t>((count + 255) / 256, 1024));
   if (nb <= 0) return cudaSuccess;

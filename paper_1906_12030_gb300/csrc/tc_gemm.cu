@@ -691,6 +691,16 @@ cudaError_t launch_gemm_tc(const TcGemmArgs& a, cudaStream_t stream) {
   }
 }
 
+__global__ void report_notconv_kernel(const int* state) {
+  if (state[0] == 0) atomicOr(&g_device_status, 1 << MERA_ENOTCONV);
+}
+
+cudaError_t launch_report_notconv(const int* state, cudaStream_t stream) {
+  count_launch();
+  report_notconv_kernel<<<1, 1, 0, stream>>>(state);
+  return cudaGetLastError();
+}
+
 cudaError_t read_device_status(int* status, bool clear) {
   cudaError_t e = cudaMemcpyFromSymbol(status, g_device_status, sizeof(int));
   if (e != cudaSuccess || !clear) return e;

@@ -34,7 +34,14 @@ struct TcGemmArgs {
 
 cudaError_t launch_gemm_tc(const TcGemmArgs& args, cudaStream_t stream);
 
-// Device status word (bit MERA_ETIMEOUT set when a bounded wait gave up).
+// Sets bit MERA_ENOTCONV of the device status word unless the Newton-Schulz
+// state state[0] says the iteration converged (used where the host cannot
+// look, e.g. inside a captured graph).
+cudaError_t launch_report_notconv(const int* state, cudaStream_t stream);
+
+// Device status word (bit MERA_ETIMEOUT set when a bounded wait gave up,
+// bit MERA_ENOTCONV when a polar update inside a captured graph did not
+// converge).
 cudaError_t read_device_status(int* status, bool clear);
 
 }  // namespace mera

@@ -1,0 +1,63 @@
+"""A sweep recorded once as a CUDA graph and replayed (mera_sweep_graph_create
+/ mera_graph_launch) must give exactly what mera_sweep gives on the same
+state: the recorded polar updates run the same device-gated Newton-Schulz
+steps, only without the host's convergence checks."""
+import numpy as np
+import pytest
+
+import mera_inputs as I
+
+torch = pytest.importorskip("torch")
+m = pytest.importorskip("paper_1906_12030_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+def _state(seed, chi):
+    layers = I.init_mera(seed, chi)
+    us = [torch.from_numpy(u).cuda().reshape(-1).contiguous() for u, _ in layers]
+    ws = [torch.from_numpy(w).cuda().contiguous() for _, w in layers]
+    rho = (torch.eye(chi ** 3, dtype=torch.float64, device="cuda") / chi ** 3).reshape(-1).contiguous()
+    return m.MeraState(us, ws, rho), us, ws, rho
+
+
+@pytest.mark.parametrize("prec,chi", [(m.PREC_F64, 4), (m.PREC_BF16X3, 8), (m.PREC_BF16X3, 16)])
+def test_graph_replays_equal_direct_sweeps(prec, chi):
+    h1_host, shift = m.mera_ising_h1(1.0)
+    h1 = torch.from_numpy(h1_host.reshape(-1)).cuda()
+    s_dir, u_dir, w_dir, r_dir = _state(3, chi)
+    s_gr, u_gr, w_gr, r_gr = _state(3, chi)
+    stream = torch.cuda.Stream()
+    e_dir = torch.empty(1, dtype=torch.float64, device="cuda")
+    e_gr = torch.empty(1, dtype=torch.float64, device="cuda")
+    ws_dir = m.workspace(m.mera_sweep_workspace_size(s_dir.chi_b, s_dir.chi_t, prec))
+    ws_gr = m.workspace(m.mera_sweep_workspace_size(s_gr.chi_b, s_gr.chi_t, prec))
+    torch.cuda.synchronize()
+    m.mera_device_status(clear=True)
+    graph = m.mera_sweep_graph(s_gr, h1, shift, 20, e_gr, prec=prec, ws=ws_gr, stream=stream)
+    try:
+        # recording computes nothing: the state is still the initial one
+        torch.cuda.synchronize()
+        assert torch.equal(r_gr, r_dir) and all(torch.equal(a, b) for a, b in zip(u_gr, u_dir))
+        for _ in range(3):
+            try:
+                m.mera_sweep(s_dir, h1, shift, 20, e_dir, prec=prec, ws=ws_dir, stream=stream)
+            except m.MeraNotConverged:
+                pass
+            graph.launch(stream)
+            stream.synchronize()
+            assert e_gr.item() == e_dir.item()
+        for a, b in zip(u_gr + w_gr + [r_gr], u_dir + w_dir + [r_dir]):
+            assert torch.equal(a, b)
+        assert m.mera_device_status(clear=True) == 0
+    finally:
+        graph.close()
+
+
+def test_graph_needs_a_stream():
+    h1_host, shift = m.mera_ising_h1(1.0)
+    h1 = torch.from_numpy(h1_host.reshape(-1)).cuda()
+    st, *_ = _state(0, 4)
+    e = torch.empty(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(m.MeraError):
+        m.mera_sweep_graph(st, h1, shift, 20, e, prec=m.PREC_F64, stream=None)

@@ -248,7 +248,10 @@ def run_native(args):
     prec = m.PRECS[args.prec]
     h1_host, shift = m.mera_ising_h1(HZ)
     h1 = torch.from_numpy(h1_host.reshape(-1)).to(dev)
-    stream = torch.cuda.current_stream(dev)
+    # a stream of our own (sweep graphs cannot be recorded on the legacy
+    # default stream); torch's own work (the L2 flush) is ordered on it too
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     def make_state(p):
@@ -619,21 +622,28 @@ def run_precision(args):
         return m.MeraState(us, ws_, rho), us, ws_, rho
 
     def run(state, schedule):
-        e = torch.empty(1, dtype=torch.float64, device=dev)
-        wss = {}
-        hist = []
-        t0 = time.perf_counter()
-        for p in schedule:
-            if p not in wss:
-                wss[p] = m.workspace(m.mera_sweep_workspace_size(state.chi_b, state.chi_t, p), dev)
-            try:
-                m.mera_sweep(state, h1, shift, N_POW, e, prec=p, ws=wss[p])
-            except m.MeraNotConverged:
-                pass
-            hist.append(e)
-            e = torch.empty(1, dtype=torch.float64, device=dev)
+        """Sweeps in the given precisions, each one a replay of a recorded
+        sweep graph of that precision (same state tensors)."""
+        stream = torch.cuda.Stream(dev)
+        graphs, es = {}, {}
+        for p in sorted(set(schedule)):
+            es[p] = torch.empty(1, dtype=torch.float64, device=dev)
+            wsp = m.workspace(m.mera_sweep_workspace_size(state.chi_b, state.chi_t, p), dev)
+            graphs[p] = m.mera_sweep_graph(state, h1, shift, N_POW, es[p], prec=p, ws=wsp, stream=stream)
+        hist = torch.empty(len(schedule), dtype=torch.float64, device=dev)
         torch.cuda.synchronize()
-        return [float(x.item()) for x in hist], time.perf_counter() - t0
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i, p in enumerate(schedule):
+                graphs[p].launch(stream)
+                hist[i:i + 1].copy_(es[p])
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if m.mera_device_status(clear=True) != 0:
+            print("note: a recorded polar update reported non-convergence", flush=True)
+        for g in graphs.values():
+            g.close()
+        return hist.cpu().tolist(), dt
 
     def evaluate(us, ws_, rho_star, p):
         """Energy per spin of a state, every map in mode p."""

@@ -56,6 +56,9 @@ def _args():
     ap.add_argument("--no-graph", action="store_true", help="skip the replayed-graph timing of the sweep")
     ap.add_argument("--sweeps", type=int, default=300, help="--case precision: optimisation sweeps per run")
     ap.add_argument("--polish", type=int, default=20, help="--case precision: FP64 sweeps after the mixed ones")
+    ap.add_argument("--grow-from", type=int, default=0,
+                    help="--case precision: also optimise at this smaller chi first, grow, then --sweeps at --chi")
+    ap.add_argument("--grow-sweeps", type=int, default=2000, help="--case precision: sweeps before growing")
     ap.add_argument("--scaling-k", type=int, default=0,
                     help="--case precision: also compare this many scaling dimensions (mixed vs FP64)")
     ap.add_argument("--case", default="sweep",
@@ -88,7 +91,7 @@ def _peak_tflops(prec: str):
 # DRAM bytes per launch of the chi^9-class GEMMs, from the ncu capture named
 # here (profiles/).  Reported only for the workload it was taken on; it must
 # be retaken (or set to None) whenever the kernel changes.
-ROOFLINE_TRAFFIC = {("bf16x3", 16): (1.119e9, "profiles/tc_gemm_bf16x3_chi16_ascend.md")}
+ROOFLINE_TRAFFIC = {}
 
 
 def _sweep_flops(m, chi):
@@ -676,6 +679,21 @@ def run_precision(args):
         dmx = scaling.scaling_dimensions(us[-1], ws_[-1], chi, k=args.scaling_k, prec=prec, tol=1e-10)
         out["mixed"]["scaling_dims_fp64"] = [float(x) for x in d64]
         out["mixed"]["scaling_dims_max_abs_err"] = float(np.max(np.abs(d64 - dmx)))
+    if args.grow_from > 0:
+        from paper_1906_12030_gb300 import grow
+
+        layers0 = I.init_mera(SEED, args.grow_from)
+        st0 = m.MeraState([torch.from_numpy(u).to(dev).reshape(-1).contiguous() for u, _ in layers0],
+                          [torch.from_numpy(w).to(dev).contiguous() for _, w in layers0],
+                          (torch.eye(args.grow_from ** 3, dtype=torch.float64, device=dev)
+                           / args.grow_from ** 3).reshape(-1).contiguous())
+        h0, t0 = run(st0, [prec] * args.grow_sweeps)
+        stg = grow.grow_state(st0, I.layer_dims(chi), seed=SEED, eps=1e-4)
+        hist_g, t_g = run(stg, [prec] * S)
+        out["grown"] = {"from_chi": args.grow_from, "sweeps_before": args.grow_sweeps,
+                        "energy_before_growth": h0[-1], "sweep_energy_last": hist_g[-1],
+                        "seconds": t0 + t_g,
+                        "energy_fp64_eval": evaluate(stg.us, stg.ws, stg.rho_star, m.PREC_F64)}
     if P > 0:
         st, us, ws_, rho = fresh()
         hist_p, t_p = run(st, [prec] * (S - P) + [m.PREC_F64] * P)

@@ -255,7 +255,7 @@ mera_status mera_flops(int op, int chi_b, int chi_t, double* flops);
  * is set when a bounded wait inside a tensor-core kernel gave up (the kernel
  * then skipped its remaining work and returned; its outputs are invalid);
  * bit (1 << MERA_ENOTCONV) when a polar update recorded in a graph (below)
- * did not converge within its recorded steps.
+ * did not converge within its step limit.
  * Synchronises with the device.  clear != 0 resets the word afterwards.
  */
 mera_status mera_device_status(int* status, int clear);
@@ -271,11 +271,12 @@ mera_status mera_device_status(int* status, int clear);
  * default stream) into *graph; nothing is computed.  Every replay then
  * performs that sweep on the same buffers: S's tensors, h1, ws and e_dev are
  * captured by address and must stay allocated (and hold the state to update)
- * until mera_graph_destroy.  Inside the recording every polar update runs
- * 40 device-gated Newton-Schulz steps with no host check (steps after
- * convergence return at once); non-convergence is reported through bit
- * MERA_ENOTCONV of mera_device_status instead of a return status.  A replay
- * gives bit-identical results to mera_sweep on the same inputs.
+ * until mera_graph_destroy.  Inside the recording every polar update is a
+ * conditional while-loop node: Newton-Schulz steps repeat until the device
+ * sees convergence (at most 100 steps, as in mera_polar_update), with no
+ * host check; non-convergence is reported through bit MERA_ENOTCONV of
+ * mera_device_status instead of a return status.  A replay gives
+ * bit-identical results to mera_sweep on the same inputs.
  * mera_graph_launch enqueues one replay on `stream` (any stream).
  */
 typedef struct mera_graph_s* mera_graph;

@@ -205,11 +205,6 @@ mera_status run_program(const OpProgram& prog, const double* const inputs[4], do
   return MERA_OK;
 }
 
-// Newton-Schulz steps recorded for a polar update inside a stream capture
-// (the Gershgorin-scaled iteration converges in 10-15 steps on the sweep's
-// environments).
-constexpr int kCaptureNsSteps = 40;
-
 // Workspace bytes of each composite operation.
 size_t op_bytes(const OpProgram& p) { return align_up(p.ws_bytes); }
 
@@ -371,14 +366,14 @@ extern "C" mera_status mera_polar_update(const double* env, int m, int n, double
   if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(MERA_EINVAL, "workspace not 256-byte aligned");
   if (!ws || ws_bytes < need) return fail(MERA_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // Inside a stream capture the host cannot look at the iteration state: a
-  // fixed number of device-gated steps is recorded instead (steps after
-  // convergence return at once) and non-convergence goes to the device
-  // status word.
+  // Inside a stream capture the host cannot look at the iteration state: the
+  // iteration is recorded as a conditional while-loop node whose body ends
+  // with a kernel that decides on the device whether to go on, and
+  // non-convergence goes to the device status word.
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return fail(MERA_ECUDA, "stream capture status");
   const bool capturing = cap != cudaStreamCaptureStatusNone;
-  if (max_iter <= 0) max_iter = capturing ? kCaptureNsSteps : 100;
+  if (max_iter <= 0) max_iter = 100;
   if (!(tol > 0)) tol = 1e-13 * std::sqrt(double(n));
   Arena ar{static_cast<char*>(ws), ws_bytes};
   double* X = reinterpret_cast<double*>(ar.take(size_t(m) * n * sizeof(double)));
@@ -394,43 +389,85 @@ extern "C" mera_status mera_polar_update(const double* env, int m, int n, double
   col_1.n = 1; col_1.dim[0] = n; col_1.stride[0] = 1;
   row_m.n = 1; row_m.dim[0] = m; row_m.stride[0] = n;
   // Device-gated iterations: once the residual is below tol, one more step
-  // runs and every later kernel returns at once.  The host looks at the
-  // state only every kCheck steps, so the stream is not drained each step.
+  // runs and every later kernel returns at once.  Without capture the host
+  // looks at the state only every kCheck steps, so the stream is not drained
+  // each step.
   constexpr int kCheck = 4;
   int* state = reinterpret_cast<int*>(scalars + 4);  // done, iterations, converged-after-this-step
   if ((e = cudaMemsetAsync(state, 0, 3 * sizeof(int), s)) != cudaSuccess) return cuda_status(e, "polar state");
-  double* buf[2] = {X, Xn};
-  int host_state[3] = {0, 0, 0};
-  double resid = 0.0;
-  for (int it = 0; it < max_iter; ++it) {
-    double* src = buf[it & 1];
-    double* dst = buf[(it + 1) & 1];
+  // G = x^T x (skipped once converged)
+  auto gram = [&](const double* x, cudaStream_t st) {
     GemmF64Args g;
     g.skip_if = state;
-    // G = X^T X
-    g.A = src; g.a_m = 1; g.a_k = n;
-    g.B = src; g.b_n = 1; g.b_k = n;
+    g.A = x; g.a_m = 1; g.a_k = n;
+    g.B = x; g.b_n = 1; g.b_k = n;
     g.M = n; g.N = n; g.K = m;
     g.C = G; g.m_dst = row_n; g.n_dst = col_1; g.alpha = 1.0; g.accumulate = 0;
-    if ((e = launch_gemm_f64(g, s)) != cudaSuccess) return cuda_status(e, "polar gemm 1");
-    if (it == 0 && (e = launch_ns_prescale(G, src, m, n, scalars + 2, s)) != cudaSuccess)
-      return cuda_status(e, "polar prescale");
-    if ((e = launch_ns_step(G, Bm, n, red, scalars + 1, tol, state, s)) != cudaSuccess)
-      return cuda_status(e, "polar step");
-    // X_next = X (3 I - X^T X) / 2
+    return launch_gemm_f64(g, st);
+  };
+  // One step src -> dst = src (3 I - G) / 2, ending with the next step's G.
+  auto step = [&](const double* src, double* dst, cudaStream_t st) {
+    cudaError_t r = launch_ns_step(G, Bm, n, red, scalars + 1, tol, state, st);
+    if (r != cudaSuccess) return r;
+    GemmF64Args g;
+    g.skip_if = state;
     g.A = src; g.a_m = n; g.a_k = 1;
     g.B = Bm; g.b_n = 1; g.b_k = n;
     g.M = m; g.N = n; g.K = n;
-    g.C = dst; g.m_dst = row_m; g.n_dst = col_1;
-    if ((e = launch_gemm_f64(g, s)) != cudaSuccess) return cuda_status(e, "polar gemm 2");
-    if ((e = launch_ns_finish(state, s)) != cudaSuccess) return cuda_status(e, "polar finish");
-    if (!capturing && ((it + 1) % kCheck == 0 || it + 1 == max_iter)) {
-      if ((e = cudaMemcpyAsync(host_state, state, sizeof host_state, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-          (e = cudaMemcpyAsync(&resid, scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return cuda_status(e, "polar state copy");
-      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e, "polar sync");
-      if (host_state[0]) break;
+    g.C = dst; g.m_dst = row_m; g.n_dst = col_1; g.alpha = 1.0; g.accumulate = 0;
+    if ((r = launch_gemm_f64(g, st)) != cudaSuccess) return r;
+    if ((r = launch_ns_finish(state, st)) != cudaSuccess) return r;
+    return gram(dst, st);
+  };
+  if ((e = gram(X, s)) != cudaSuccess) return cuda_status(e, "polar gemm");
+  if ((e = launch_ns_prescale(G, X, m, n, scalars + 2, s)) != cudaSuccess) return cuda_status(e, "polar prescale");
+  int host_state[3] = {0, 0, 0};
+  double resid = 0.0;
+  if (!capturing) {
+    double* buf[2] = {X, Xn};
+    for (int it = 0; it < max_iter; ++it) {
+      if ((e = step(buf[it & 1], buf[(it + 1) & 1], s)) != cudaSuccess) return cuda_status(e, "polar step");
+      if ((it + 1) % kCheck == 0 || it + 1 == max_iter) {
+        if ((e = cudaMemcpyAsync(host_state, state, sizeof host_state, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&resid, scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+          return cuda_status(e, "polar state copy");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e, "polar sync");
+        if (host_state[0]) break;
+      }
     }
+  } else {
+    // while (not converged and fewer than max_iter steps): X -> Xn -> X
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, &edges, &nd)) != cudaSuccess)
+      return cuda_status(e, "capture info");
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+      return cuda_status(e, "conditional handle");
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t loop = nullptr;
+    if ((e = cudaGraphAddNode(&loop, cg, deps, edges, nd, &p)) != cudaSuccess) return cuda_status(e, "while node");
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    cudaStream_t bs = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking)) != cudaSuccess) return cuda_status(e, "body stream");
+    e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) e = step(X, Xn, bs);
+    if (e == cudaSuccess) e = step(Xn, X, bs);
+    if (e == cudaSuccess) e = launch_ns_continue(state, h, max_iter, bs);
+    cudaGraph_t got = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(bs, &got);
+    cudaStreamDestroy(bs);
+    if (e != cudaSuccess || e2 != cudaSuccess) return cuda_status(e != cudaSuccess ? e : e2, "while body");
+    if ((e = cudaStreamUpdateCaptureDependencies(s, &loop, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+      return cuda_status(e, "capture dependencies");
   }
   e = launch_ns_output(X, Xn, state, out, int64_t(m) * n, s);  // -X of the last step, chosen on the device
   if (e != cudaSuccess) return cuda_status(e, "polar output");

@@ -61,6 +61,9 @@ cudaError_t launch_ns_finish(int* state, cudaStream_t stream);
 // out = -(state[1] odd ? x1 : x0): the polar result, selected on the device.
 cudaError_t launch_ns_output(const double* x0, const double* x1, const int* state, double* out, int64_t count,
                              cudaStream_t stream);
+// Sets the conditional handle of a recorded while loop to (state[0] == 0 and
+// state[1] < max_iter).
+cudaError_t launch_ns_continue(const int* state, cudaGraphConditionalHandle h, int max_iter, cudaStream_t stream);
 cudaError_t launch_scale_copy(const double* src, double* dst, int64_t count, double alpha,
                               cudaStream_t stream);
 

@@ -656,6 +656,18 @@ cudaError_t launch_ns_output(const double* x0, const double* x1, const int* stat
   return cudaGetLastError();
 }
 
+// Last kernel of a recorded Newton-Schulz loop body: go on while not
+// converged and fewer than max_iter steps have run.
+__global__ void ns_continue_kernel(const int* state, cudaGraphConditionalHandle h, int max_iter) {
+  cudaGraphSetConditional(h, (state[0] == 0 && state[1] < max_iter) ? 1u : 0u);
+}
+
+cudaError_t launch_ns_continue(const int* state, cudaGraphConditionalHandle h, int max_iter, cudaStream_t stream) {
+  count_launch();
+  ns_continue_kernel<<<1, 1, 0, stream>>>(state, h, max_iter);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scale_copy(const double* src, double* dst, int64_t count, double alpha, cudaStream_t stream) {
   const int nb = int(std::min<int64_t>((count + 255) / 256, 1024));
   if (nb <= 0) return cudaSuccess;

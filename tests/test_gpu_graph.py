@@ -61,3 +61,43 @@ def test_graph_needs_a_stream():
     e = torch.empty(1, dtype=torch.float64, device="cuda")
     with pytest.raises(m.MeraError):
         m.mera_sweep_graph(st, h1, shift, 20, e, prec=m.PREC_F64, stream=None)
+
+
+def test_grown_mera_contains_the_smaller_one():
+    """chi = 4 -> 6 growth: the new tensors are isometric / unitary to binary64
+    accuracy, their leading blocks are the old tensors up to the perturbation,
+    and the grown MERA's energy after one sweep is no higher than the old
+    one's."""
+    from paper_1906_12030_gb300 import grow
+
+    h1_host, shift = m.mera_ising_h1(1.0)
+    h1 = torch.from_numpy(h1_host.reshape(-1)).cuda()
+    st, *_ = _state(5, 4)
+    e = torch.empty(1, dtype=torch.float64, device="cuda")
+    for _ in range(30):
+        try:
+            m.mera_sweep(st, h1, shift, 20, e, prec=m.PREC_F64)
+        except m.MeraNotConverged:
+            pass
+    e_small = e.item()
+    big = grow.grow_state(st, I.layer_dims(6), seed=1, eps=1e-4)
+    for (cb, ct), (nb, nt), u, w, u2, w2 in zip(zip(st.chi_b, st.chi_t), zip(big.chi_b, big.chi_t), st.us, st.ws,
+                                               big.us, big.ws):
+        U = u2.reshape(nb * nb, nb * nb)
+        W = w2.reshape(nb * nb, nt)
+        eye_u = torch.eye(nb * nb, dtype=torch.float64, device="cuda")
+        eye_w = torch.eye(nt, dtype=torch.float64, device="cuda")
+        assert float((U.T @ U - eye_u).abs().max()) < 1e-12
+        assert float((W.T @ W - eye_w).abs().max()) < 1e-12
+        old_u = u.reshape((cb,) * 4)
+        old_w = w.reshape(cb, cb, ct)
+        assert float((u2.reshape((nb,) * 4)[:cb, :cb, :cb, :cb] - old_u).abs().max()) < 1e-2
+        assert float((w2.reshape(nb, nb, nt)[:cb, :cb, :ct] - old_w).abs().max()) < 1e-2
+    try:
+        m.mera_sweep(big, h1, shift, 20, e, prec=m.PREC_F64)
+    except m.MeraNotConverged:
+        pass
+    e_big = e.item()
+    # variational: above the exact energy, and the warm start loses nothing
+    # (one more sweep with more freedom lowers it further)
+    assert -4.0 / np.pi - 1e-9 <= e_big <= e_small + 1e-4

@@ -198,3 +198,47 @@ def test_chi16_bf16x3_sampled_rows_and_properties():
     m.mera_ascend(eye, ud, wd, chi, chi, a, prec=prec)
     err = (a.reshape(chi ** 3, chi ** 3) - torch.eye(chi ** 3, dtype=torch.float64, device="cuda")).abs().max()
     assert float(err) < MAP_TOL[prec]
+
+
+def _dot(a, b, chunk=1 << 30):
+    """Dot product of long vectors (the BLAS dot takes at most 2^31 - 1)."""
+    return sum(float(torch.dot(a[i:i + chunk], b[i:i + chunk])) for i in range(0, a.numel(), chunk))
+
+
+@pytest.mark.parametrize("chi", [32, 40])
+def test_full_size_properties(chi):
+    """chi = 32 and 40 (the precision workload's largest sizes; chi = 40 runs
+    the sliced chi^9 pairs), where the oracle cannot run: properties that hold
+    at any size, on seeded operators drawn on the device.
+    - A(1) = 1 (Eq. iso, Eq. unitarity);
+    - tr D(rho) = tr rho;
+    - duality <A(h), rho> = <h, D(rho)> (D is the adjoint of A)."""
+    prec = m.PREC_BF16X3
+    rng = np.random.default_rng(chi)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    ud, wd = _cuda(u).reshape(-1), _cuda(w).reshape(-1)
+    n3 = chi ** 3
+    g = torch.Generator(device="cuda")
+    g.manual_seed(chi)
+    ws = m.workspace(max(m.mera_workspace_size(op, chi, chi, prec) for op in (m.OP_ASCEND, m.OP_DESCEND)))
+    out = torch.empty(n3 * n3, dtype=torch.float64, device="cuda")
+    x = torch.eye(n3, dtype=torch.float64, device="cuda").reshape(-1)
+    m.mera_ascend(x, ud, wd, chi, chi, out, prec=prec, ws=ws)
+    err = float((out.reshape(n3, n3).diagonal() - 1.0).abs().max())
+    out.reshape(n3, n3).diagonal().zero_()
+    err = max(err, float(out.abs().max()))
+    assert err < MAP_TOL[prec], err
+    # duality and trace with random (non-symmetric) h and rho
+    x.normal_(generator=g)  # h
+    rho = torch.empty_like(x).normal_(generator=g)
+    m.mera_ascend(x, ud, wd, chi, chi, out, prec=prec, ws=ws)
+    lhs = _dot(out, rho)
+    hn, rn = float(x.norm()), float(rho.norm())
+    m.mera_descend(rho, ud, wd, chi, chi, out, prec=prec, ws=ws)
+    rhs = _dot(x, out)
+    # both sides carry the maps' error relative to |h| |rho|
+    assert abs(lhs - rhs) <= MAP_TOL[prec] * hn * rn, (lhs, rhs)
+    tr_in = float(rho.reshape(n3, n3).diagonal().sum())
+    tr_out = float(out.reshape(n3, n3).diagonal().sum())
+    assert abs(tr_out - tr_in) <= MAP_TOL[prec] * float(rho.reshape(n3, n3).diagonal().abs().sum()) + 1e-9
+    torch.cuda.synchronize()

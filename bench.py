@@ -56,6 +56,8 @@ def _args():
     ap.add_argument("--no-graph", action="store_true", help="skip the replayed-graph timing of the sweep")
     ap.add_argument("--sweeps", type=int, default=300, help="--case precision: optimisation sweeps per run")
     ap.add_argument("--polish", type=int, default=20, help="--case precision: FP64 sweeps after the mixed ones")
+    ap.add_argument("--riemannian-eta", type=float, default=0.0,
+                    help="--case precision: also run --sweeps Riemannian-gradient sweeps with this step size")
     ap.add_argument("--grow-from", type=int, default=0,
                     help="--case precision: also optimise at this smaller chi first, grow, then --sweeps at --chi")
     ap.add_argument("--grow-sweeps", type=int, default=2000, help="--case precision: sweeps before growing")
@@ -679,6 +681,24 @@ def run_precision(args):
         dmx = scaling.scaling_dimensions(us[-1], ws_[-1], chi, k=args.scaling_k, prec=prec, tol=1e-10)
         out["mixed"]["scaling_dims_fp64"] = [float(x) for x in d64]
         out["mixed"]["scaling_dims_max_abs_err"] = float(np.max(np.abs(d64 - dmx)))
+    if args.riemannian_eta > 0:
+        st, us, ws_, rho = fresh()
+        er = torch.empty(S, dtype=torch.float64, device=dev)
+        wsr = m.workspace(m.mera_sweep_workspace_size(st.chi_b, st.chi_t, prec), dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(S):
+            try:
+                m.mera_sweep_riemannian(st, h1, shift, N_POW, args.riemannian_eta, er[i:i + 1], prec=prec, ws=wsr)
+            except m.MeraNotConverged:
+                pass
+        torch.cuda.synchronize()
+        hr = er.cpu().tolist()
+        out["riemannian"] = {"eta": args.riemannian_eta, "sweep_energy_last": hr[-1],
+                             "sweep_energy_at_quarter": hr[max(0, S // 4 - 1)],
+                             "seconds": time.perf_counter() - t0,
+                             "energy_fp64_eval": evaluate(us, ws_, rho, m.PREC_F64)}
+        out["mixed"]["sweep_energy_at_quarter"] = hist_m[max(0, S // 4 - 1)]
     if args.grow_from > 0:
         from paper_1906_12030_gb300 import grow
 

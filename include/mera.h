@@ -231,6 +231,30 @@ mera_status mera_sweep_batch(mera_state* states, int n, const double* const* h1,
                              int n_pow, int prec, void* const* ws, const size_t* ws_bytes, double* e_dev,
                              void* const* streams, int n_threads);
 
+/*
+ * Riemannian alternative to the polar update (the paper notes gradients can be
+ * obtained by automatic differentiation, Fig. A1 caption; the update itself is
+ * the standard Stiefel-manifold step, not the paper's method).
+ *
+ * mera_stiefel_step: X (m x n, isometric: X^T X = 1, m >= n) and a Euclidean
+ * gradient G (m x n), both row-major binary64 device arrays.  Writes
+ *   out = polar(X - eta (G - X sym(X^T G))),  sym(A) = (A + A^T) / 2,
+ * i.e. one gradient step of length eta along the Riemannian gradient of the
+ * embedded metric, retracted to the manifold by the polar factor (computed
+ * by the polar update's Newton-Schulz iteration).  out may alias X, not G.
+ * Scratch: mera_stiefel_workspace_size(m, n).  MERA_ENOTCONV as for
+ * mera_polar_update.
+ *
+ * mera_sweep_riemannian: mera_sweep with every tensor update replaced by
+ * mera_stiefel_step(X, 2 Gamma, eta) (2 Gamma is the energy's gradient for
+ * symmetric h and rho).  Same workspace as mera_sweep.
+ */
+mera_status mera_stiefel_workspace_size(int m, int n, size_t* bytes);
+mera_status mera_stiefel_step(const double* X, const double* G, int m, int n, double eta, double* out, void* ws,
+                              size_t ws_bytes, void* stream);
+mera_status mera_sweep_riemannian(mera_state* S, const double* h1, double shift, int n_pow, int prec, double eta,
+                                  void* ws, size_t ws_bytes, double* e_dev, void* stream);
+
 /* Scratch bytes for mera_sweep on a state with these dimensions. */
 mera_status mera_sweep_workspace_size(int n_layers, const int* chi_b, const int* chi_t, int prec,
                                       size_t* bytes);

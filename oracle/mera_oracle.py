@@ -222,6 +222,20 @@ def polar_update(env: np.ndarray, n_lower: int) -> np.ndarray:
     return (-(uu @ vt)).reshape(shape)
 
 
+def stiefel_step(x: np.ndarray, g: np.ndarray, eta: float) -> np.ndarray:
+    """One Riemannian gradient step on the Stiefel manifold, embedded metric
+    (the update the paper's Fig. A1 caption points to when it mentions
+    gradients; not the paper's own SVD update): the Euclidean gradient g is
+    projected onto the tangent space at the isometry x,
+        r = g - x sym(x^T g),   sym(a) = (a + a^T) / 2,
+    and x - eta r is retracted to the manifold by its polar factor (SVD).
+    x, g: m x n matrices (m >= n)."""
+    a = x.T @ g
+    r = g - x @ (0.5 * (a + a.T))
+    uu, _, vt = np.linalg.svd(x - eta * r, full_matrices=False)
+    return uu @ vt
+
+
 def update_u(h, rho, u, w):
     return polar_update(env_u(h, rho, u, w), 2)
 
@@ -266,8 +280,11 @@ def identity_density(chi: int) -> np.ndarray:
 # Sweep (Sec. II C).  layers = [(u1, w1), (u2, w2), (u3, w3)], bottom first;
 # the last one is the scale-invariant layer.
 # ---------------------------------------------------------------------------
-def sweep(layers, h1, shift, rho_star, n_pow: int = 20):
+def sweep(layers, h1, shift, rho_star, n_pow: int = 20, eta: float | None = None):
     """One optimisation sweep.  Returns (new_layers, rho_star, e_per_spin).
+    eta None: the paper's SVD (polar) update of each tensor; eta > 0: a
+    Riemannian gradient step of size eta instead (stiefel_step with the
+    energy's gradient 2 Gamma, the environments being half the gradient).
 
     1. ascend h1 through the transitional layers (old tensors),
     2. rho* <- n_pow power iterations of the SI descending map (warm start),
@@ -289,8 +306,15 @@ def sweep(layers, h1, shift, rho_star, n_pow: int = 20):
     rho_above = rho_star
     for tau in range(n - 1, -1, -1):
         u, w = layers[tau]
-        u = update_u(hs[tau], rho_above, u, w)
-        w = update_w(hs[tau], rho_above, u, w)
+        if eta is None:
+            u = update_u(hs[tau], rho_above, u, w)
+            w = update_w(hs[tau], rho_above, u, w)
+        else:
+            cb, ct = w.shape[0], w.shape[2]
+            gu = 2.0 * env_u(hs[tau], rho_above, u, w)
+            u = stiefel_step(u.reshape(cb * cb, cb * cb), gu.reshape(cb * cb, cb * cb), eta).reshape(u.shape)
+            gw = 2.0 * env_w(hs[tau], rho_above, u, w)
+            w = stiefel_step(w.reshape(cb * cb, ct), gw.reshape(cb * cb, ct), eta).reshape(w.shape)
         layers[tau] = (u, w)
         if 0 < tau < n - 1:
             # rho_{tau*} = rho* sits on top of the last transitional layer;

@@ -20,7 +20,8 @@ __all__ = [
     "mera_energy", "mera_ising_h1", "mera_sweep", "mera_sweep_workspace_size", "mera_plan_json", "mera_flops",
     "workspace", "MeraState", "mera_launch_count", "mera_profile_enable", "mera_profile_read",
     "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE", "mera_device_status", "mera_gemm_test",
-    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_sweep_batch", "mera_set_slice_bytes", "MeraGraph", "mera_sweep_graph",
+    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_sweep_batch", "mera_set_slice_bytes", "MeraGraph", "mera_sweep_graph", "mera_stiefel_step",
+    "mera_stiefel_workspace_size", "mera_sweep_riemannian",
 ]
 
 PREC_F64, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3, 4
@@ -102,6 +103,9 @@ def library():
             "mera_sweep_graph_create": ([ctypes.POINTER(_State), vp, d, i, i, vp, sz, vp, vp, ctypes.POINTER(vp)], i),
             "mera_graph_launch": ([vp, vp], i),
             "mera_graph_destroy": ([vp], i),
+            "mera_stiefel_workspace_size": ([i, i, ctypes.POINTER(sz)], i),
+            "mera_stiefel_step": ([vp, vp, i, i, d, vp, vp, sz, vp], i),
+            "mera_sweep_riemannian": ([ctypes.POINTER(_State), vp, d, i, i, d, vp, sz, vp, vp], i),
             "mera_sweep_batch": ([ctypes.POINTER(_State), i, ctypes.POINTER(vp), ctypes.POINTER(d), i, i,
                                   ctypes.POINTER(vp), ctypes.POINTER(sz), vp, ctypes.POINTER(vp), i], i),
             "mera_profile_enable": ([i], i),
@@ -354,6 +358,33 @@ def mera_sweep_graph(state: MeraState, h1, shift, n_pow, e_out, prec=PREC_F64, w
                                              n_pow, prec, p, n, _f64(e_out, 1, "e_out"), _stream(stream),
                                              ctypes.byref(h)))
     return MeraGraph(h, (state, h1, e_out, ws))
+
+
+def mera_stiefel_workspace_size(m: int, n: int) -> int:
+    out = ctypes.c_size_t()
+    _check(library().mera_stiefel_workspace_size(m, n, ctypes.byref(out)))
+    return out.value
+
+
+def mera_stiefel_step(x, g, m, n, eta, out, ws=None, stream=None):
+    """out = polar(X - eta (G - X sym(X^T G))) for an m x n isometry X."""
+    if ws is None:
+        ws = workspace(mera_stiefel_workspace_size(m, n), x.device)
+    p, nb = _ws(ws)
+    _check(library().mera_stiefel_step(_f64(x, m * n, "x"), _f64(g, m * n, "g"), m, n, float(eta),
+                                       _f64(out, m * n, "out"), p, nb, _stream(stream)))
+    return out
+
+
+def mera_sweep_riemannian(state: MeraState, h1, shift, n_pow, eta, e_out, prec=PREC_F64, ws=None, stream=None):
+    """mera_sweep with Riemannian gradient steps of size eta instead of polar updates."""
+    if ws is None:
+        ws = workspace(mera_sweep_workspace_size(state.chi_b, state.chi_t, prec), h1.device)
+    p, n = _ws(ws)
+    st = state._c()
+    _check(library().mera_sweep_riemannian(ctypes.byref(st), _f64(h1, state.chi_b[0] ** 6, "h1"), float(shift), n_pow,
+                                           prec, float(eta), p, n, _f64(e_out, 1, "e_out"), _stream(stream)))
+    return e_out
 
 
 def mera_launch_count() -> int:

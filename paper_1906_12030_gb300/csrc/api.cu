@@ -130,6 +130,8 @@ struct Arena {
     used += align_up(bytes);
     return p;
   }
+  char* ptr() const { return base + used; }
+  size_t left() const { return used <= cap ? cap - used : 0; }
 };
 
 // Execute a contraction program; inputs[slot] are device pointers.
@@ -352,6 +354,12 @@ static size_t polar_bytes(int m, int n) {
          kReduceBytes;
 }
 
+// Stiefel step: A, S (n x n), T, Yneg (m x n), then the polar update's scratch.
+static size_t stiefel_bytes(int m, int n) {
+  return 2 * align_up(size_t(n) * n * sizeof(double)) + 2 * align_up(size_t(m) * n * sizeof(double)) +
+         polar_bytes(m, n);
+}
+
 extern "C" mera_status mera_polar_workspace_size(int m, int n, size_t* bytes) {
   if (!bytes || m < 1 || n < 1 || m < n || m > 1 << 16) return fail(MERA_EINVAL, "bad polar sizes");
   *bytes = polar_bytes(m, n);
@@ -480,6 +488,50 @@ extern "C" mera_status mera_polar_update(const double* env, int m, int n, double
   return MERA_OK;
 }
 
+extern "C" mera_status mera_stiefel_workspace_size(int m, int n, size_t* bytes) {
+  if (!bytes || m < 1 || n < 1 || m < n) return fail(MERA_EINVAL, "bad stiefel sizes");
+  *bytes = stiefel_bytes(m, n);
+  return MERA_OK;
+}
+
+extern "C" mera_status mera_stiefel_step(const double* X, const double* G, int m, int n, double eta, double* out,
+                                         void* ws, size_t ws_bytes, void* stream) {
+  if (!X || !G || !out || G == out) return fail(MERA_EINVAL, "bad stiefel pointers");
+  if (m < 1 || n < 1 || m < n || m > 1 << 16) return fail(MERA_EINVAL, "stiefel step needs m >= n >= 1");
+  if (!(eta >= 0.0) || !std::isfinite(eta)) return fail(MERA_EINVAL, "bad step size");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(MERA_EINVAL, "workspace not 256-byte aligned");
+  if (!ws || ws_bytes < stiefel_bytes(m, n)) return fail(MERA_ENOMEM, "stiefel workspace too small");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Arena ar{static_cast<char*>(ws), ws_bytes};
+  double* A = reinterpret_cast<double*>(ar.take(size_t(n) * n * sizeof(double)));
+  double* S = reinterpret_cast<double*>(ar.take(size_t(n) * n * sizeof(double)));
+  double* T = reinterpret_cast<double*>(ar.take(size_t(m) * n * sizeof(double)));
+  double* Y = reinterpret_cast<double*>(ar.take(size_t(m) * n * sizeof(double)));
+  LegMap row_n, col_1, row_m;
+  row_n.n = 1; row_n.dim[0] = n; row_n.stride[0] = n;
+  col_1.n = 1; col_1.dim[0] = n; col_1.stride[0] = 1;
+  row_m.n = 1; row_m.dim[0] = m; row_m.stride[0] = n;
+  GemmF64Args g;
+  // A = X^T G
+  g.A = X; g.a_m = 1; g.a_k = n;
+  g.B = G; g.b_n = 1; g.b_k = n;
+  g.M = n; g.N = n; g.K = m;
+  g.C = A; g.m_dst = row_n; g.n_dst = col_1; g.alpha = 1.0; g.accumulate = 0;
+  cudaError_t e = launch_gemm_f64(g, s);
+  if (e == cudaSuccess) e = launch_stiefel_sym(A, S, n, s);
+  if (e != cudaSuccess) return cuda_status(e, "stiefel sym");
+  // T = X S
+  g.A = X; g.a_m = n; g.a_k = 1;
+  g.B = S; g.b_n = 1; g.b_k = n;
+  g.M = m; g.N = n; g.K = n;
+  g.C = T; g.m_dst = row_m; g.n_dst = col_1;
+  e = launch_gemm_f64(g, s);
+  if (e == cudaSuccess) e = launch_stiefel_combine(X, G, T, Y, int64_t(m) * n, eta, s);
+  if (e != cudaSuccess) return cuda_status(e, "stiefel combine");
+  // retraction: polar(X - eta (G - T)) = -polar_update(-(X - eta (G - T)))
+  return mera_polar_update(Y, m, n, out, 0, 0.0, ar.ptr(), ar.left(), stream);
+}
+
 // ---------------------------------------------------------------------------
 // Sweep.
 // ---------------------------------------------------------------------------
@@ -513,7 +565,7 @@ mera_status sweep_layout(int n_layers, const int* chi_b, const int* chi_t, int p
       map_bytes = std::max(map_bytes, op_bytes(*p));
     }
     const int64_t eb = int64_t(chi_b[t]) * chi_b[t];
-    map_bytes = std::max(map_bytes, polar_bytes(int(eb), int(eb)));
+    map_bytes = std::max(map_bytes, stiefel_bytes(int(eb), int(eb)));  // >= polar_bytes
     size_t fp = 0;
     if (t == n_layers - 1) {
       ws_size_impl(MERA_OP_FIXED_POINT, chi_b[t], chi_t[t], prec, &fp);
@@ -558,8 +610,11 @@ extern "C" mera_status mera_sweep_workspace_size(int n_layers, const int* chi_b,
   return MERA_OK;
 }
 
-extern "C" mera_status mera_sweep(mera_state* S, const double* h1, double shift, int n_pow, int prec, void* ws,
-                                  size_t ws_bytes, double* e_dev, void* stream) {
+// One sweep; update 0: polar (SVD) update of every tensor (Fig. 5); update
+// 1: one Riemannian gradient step on the Stiefel manifold with step size
+// eta (gradient 2 Gamma), retracted by the polar factor.
+static mera_status sweep_impl(mera_state* S, const double* h1, double shift, int n_pow, int prec, void* ws,
+                              size_t ws_bytes, double* e_dev, void* stream, int update, double eta) {
   if (!S || !h1 || !e_dev) return fail(MERA_EINVAL, "null argument");
   const int n = S->n_layers;
   SweepLayout L;
@@ -596,12 +651,14 @@ extern "C" mera_status mera_sweep(mera_state* S, const double* h1, double shift,
     const int cb = S->chi_b[t], ct = S->chi_t[t];
     st = mera_env_u(hs[t], rho_above, S->u[t], S->w[t], cb, ct, env, prec, mws, mb, stream);
     if (st != MERA_OK) return st;
-    st = mera_polar_update(env, cb * cb, cb * cb, S->u[t], 0, 0.0, mws, mb, stream);
+    st = update ? mera_stiefel_step(S->u[t], env, cb * cb, cb * cb, 2.0 * eta, S->u[t], mws, mb, stream)
+                : mera_polar_update(env, cb * cb, cb * cb, S->u[t], 0, 0.0, mws, mb, stream);
     if (st == MERA_ENOTCONV) notconv = true;
     else if (st != MERA_OK) return st;
     st = mera_env_w(hs[t], rho_above, S->u[t], S->w[t], cb, ct, env, prec, mws, mb, stream);
     if (st != MERA_OK) return st;
-    st = mera_polar_update(env, cb * cb, ct, S->w[t], 0, 0.0, mws, mb, stream);
+    st = update ? mera_stiefel_step(S->w[t], env, cb * cb, ct, 2.0 * eta, S->w[t], mws, mb, stream)
+                : mera_polar_update(env, cb * cb, ct, S->w[t], 0, 0.0, mws, mb, stream);
     if (st == MERA_ENOTCONV) notconv = true;
     else if (st != MERA_OK) return st;
     if (t > 0 && t < n - 1) {  // rho* sits on top of the last transitional layer
@@ -622,6 +679,17 @@ extern "C" mera_status mera_sweep(mera_state* S, const double* h1, double shift,
   if (st != MERA_OK) return st;
   if (notconv) return fail(MERA_ENOTCONV, "a polar update hit its iteration cap");
   return MERA_OK;
+}
+
+extern "C" mera_status mera_sweep(mera_state* S, const double* h1, double shift, int n_pow, int prec, void* ws,
+                                  size_t ws_bytes, double* e_dev, void* stream) {
+  return sweep_impl(S, h1, shift, n_pow, prec, ws, ws_bytes, e_dev, stream, 0, 0.0);
+}
+
+extern "C" mera_status mera_sweep_riemannian(mera_state* S, const double* h1, double shift, int n_pow, int prec,
+                                             double eta, void* ws, size_t ws_bytes, double* e_dev, void* stream) {
+  if (!(eta > 0.0) || !std::isfinite(eta)) return fail(MERA_EINVAL, "bad step size");
+  return sweep_impl(S, h1, shift, n_pow, prec, ws, ws_bytes, e_dev, stream, 1, eta);
 }
 
 // ---------------------------------------------------------------------------

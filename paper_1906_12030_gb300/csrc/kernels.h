@@ -61,6 +61,11 @@ cudaError_t launch_ns_finish(int* state, cudaStream_t stream);
 // out = -(state[1] odd ? x1 : x0): the polar result, selected on the device.
 cudaError_t launch_ns_output(const double* x0, const double* x1, const int* state, double* out, int64_t count,
                              cudaStream_t stream);
+// Stiefel gradient step helpers: S = (A + A^T)/2 (n x n) and
+// Yneg = eta (G - T) - X (count elements).
+cudaError_t launch_stiefel_sym(const double* A, double* S, int64_t n, cudaStream_t stream);
+cudaError_t launch_stiefel_combine(const double* X, const double* G, const double* T, double* Yneg, int64_t count,
+                                   double eta, cudaStream_t stream);
 // Sets the conditional handle of a recorded while loop to (state[0] == 0 and
 // state[1] < max_iter).
 cudaError_t launch_ns_continue(const int* state, cudaGraphConditionalHandle h, int max_iter, cudaStream_t stream);

@@ -656,6 +656,39 @@ cudaError_t launch_ns_output(const double* x0, const double* x1, const int* stat
   return cudaGetLastError();
 }
 
+// Riemannian gradient step on the Stiefel manifold (embedded metric):
+// with A = X^T G, S = (A + A^T) / 2 and T = X S, the step direction is
+// G - T; the kernel writes Yneg = -(X - eta (G - T)) for the polar retraction
+// (the polar update returns -polar(-Y) = polar(Y)).
+__global__ void __launch_bounds__(256) stiefel_sym_kernel(const double* __restrict__ A, double* S, int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n * n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / n, c = i - r * n;
+    S[i] = 0.5 * (A[i] + A[c * n + r]);
+  }
+}
+
+__global__ void __launch_bounds__(256) stiefel_combine_kernel(const double* __restrict__ X, const double* __restrict__ G,
+                                                              const double* __restrict__ T, double* Yneg, int64_t count,
+                                                              double eta) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x)
+    Yneg[i] = eta * (G[i] - T[i]) - X[i];
+}
+
+cudaError_t launch_stiefel_sym(const double* A, double* S, int64_t n, cudaStream_t stream) {
+  const int nb = int(std::min<int64_t>((n * n + 255) / 256, 1024));
+  count_launch();
+  stiefel_sym_kernel<<<nb, 256, 0, stream>>>(A, S, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stiefel_combine(const double* X, const double* G, const double* T, double* Yneg, int64_t count,
+                                   double eta, cudaStream_t stream) {
+  const int nb = int(std::min<int64_t>((count + 255) / 256, 1024));
+  count_launch();
+  stiefel_combine_kernel<<<nb, 256, 0, stream>>>(X, G, T, Yneg, count, eta);
+  return cudaGetLastError();
+}
+
 // Last kernel of a recorded Newton-Schulz loop body: go on while not
 // converged and fewer than max_iter steps have run.
 __global__ void ns_continue_kernel(const int* state, cudaGraphConditionalHandle h, int max_iter) {

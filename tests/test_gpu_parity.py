@@ -149,6 +149,48 @@ def test_sweeps_match_oracle_chi4():
     assert _err(rho.cpu().numpy().reshape(orho.shape), orho) < 1e-9
 
 
+@pytest.mark.parametrize("mm,nn", [(16, 16), (64, 8), (256, 16), (300, 7)])
+def test_stiefel_step_f64(mm, nn):
+    rng = np.random.default_rng(mm + 7 * nn)
+    x = I.random_isometry(rng, mm, nn)
+    g = rng.standard_normal((mm, nn))
+    out = torch.empty(mm * nn, dtype=torch.float64, device="cuda")
+    m.mera_stiefel_step(_cuda(x).reshape(-1), _cuda(g).reshape(-1), mm, nn, 0.2, out)
+    want = O.stiefel_step(x, g, 0.2)
+    got = out.cpu().numpy().reshape(mm, nn)
+    assert np.abs(got - want).max() < 1e-10
+    # in place (out aliases X) gives the same
+    xd = _cuda(x).reshape(-1).clone()
+    m.mera_stiefel_step(xd, _cuda(g).reshape(-1), mm, nn, 0.2, xd)
+    assert np.abs(xd.cpu().numpy().reshape(mm, nn) - want).max() < 1e-10
+
+
+def test_riemannian_sweeps_match_oracle_chi3():
+    chi, n_sweeps, eta = 3, 3, 0.1
+    layers = I.init_mera(2, chi)
+    h1, shift = O.ising_h1(1.0)
+    ol = [(u.copy(), w.copy()) for u, w in layers]
+    orho = O.identity_density(chi)
+    oes = []
+    for _ in range(n_sweeps):
+        ol, orho, e_ = O.sweep(ol, h1, shift, orho, 20, eta=eta)
+        oes.append(e_)
+    us = [_cuda(u).reshape(-1).clone() for u, _ in layers]
+    ws = [_cuda(w).clone() for _, w in layers]
+    rho = _cuda(O.identity_density(chi)).reshape(-1).clone()
+    st = m.MeraState(us, ws, rho)
+    e = torch.empty(1, dtype=torch.float64, device="cuda")
+    h1d = _cuda(h1).reshape(-1)
+    es = []
+    for _ in range(n_sweeps):
+        m.mera_sweep_riemannian(st, h1d, shift, 20, eta, e)
+        es.append(e.item())
+    np.testing.assert_allclose(es, oes, rtol=1e-10, atol=0)
+    for (ou, ow), u, w in zip(ol, us, ws):
+        assert np.abs(u.cpu().numpy().reshape(ou.shape) - ou).max() < 1e-9
+        assert np.abs(w.cpu().numpy().reshape(ow.shape) - ow).max() < 1e-9
+
+
 # --------------------------------------------------------------------------
 # Full size (chi = 16, the benchmarked workload): sampled rows and properties.
 # --------------------------------------------------------------------------

@@ -325,3 +325,66 @@ def test_sweeps_lower_energy_and_respect_variational_bound():
         wm = w.reshape(w.shape[0] ** 2, -1)
         assert np.abs(um.T @ um - np.eye(um.shape[1])).max() < 1e-12
         assert np.abs(wm.T @ wm - np.eye(wm.shape[1])).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Riemannian (Stiefel) gradient step: pinned by properties, not a retyping.
+# ---------------------------------------------------------------------------
+def test_stiefel_step_stays_on_the_manifold_and_fixes_zero_steps():
+    rng = np.random.default_rng(41)
+    x = I.random_isometry(rng, 9, 4)
+    g = rng.standard_normal((9, 4))
+    y = O.stiefel_step(x, g, 0.3)
+    assert np.abs(y.T @ y - np.eye(4)).max() < 1e-13
+    assert np.abs(O.stiefel_step(x, g, 0.0) - x).max() < 1e-13
+
+
+def test_stiefel_direction_is_tangent():
+    """The step direction (y(-eta) - y(eta)) / (2 eta) -> the projected
+    gradient r as eta -> 0, and r must lie in the tangent space:
+    x^T r + r^T x = 0."""
+    rng = np.random.default_rng(42)
+    x = I.random_isometry(rng, 16, 5)
+    g = rng.standard_normal((16, 5))
+    eta = 1e-5
+    r = (O.stiefel_step(x, g, -eta) - O.stiefel_step(x, g, eta)) / (2 * eta)
+    assert np.abs(x.T @ r + r.T @ x).max() < 1e-8
+    # and it is the gradient's tangent part: <g - r, t> = 0 for tangent t
+    k = rng.standard_normal((5, 5))
+    t = x @ (k - k.T) + (np.eye(16) - x @ x.T) @ rng.standard_normal((16, 5))
+    assert abs(np.sum((g - r) * t)) < 1e-5 * np.abs(g).sum()
+
+
+def test_stiefel_step_descends_the_mera_energy_at_the_predicted_rate():
+    """f(w) = tr(A(h) rho) with symmetric h, rho has gradient 2 Gamma_w; a step
+    of size eta along the Riemannian gradient changes f by -eta |r|^2 to
+    first order (central difference), r the projected gradient."""
+    rng = np.random.default_rng(43)
+    chi = 2
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    h, rho = I.random_operator(rng, chi), I.random_density(rng, chi)
+    x = w.reshape(chi * chi, chi)
+    g = (2.0 * O.env_w(h, rho, u, w)).reshape(chi * chi, chi)
+    a = x.T @ g
+    r = g - x @ (0.5 * (a + a.T))
+    eta = 1e-5
+
+    def f(xx):
+        return O.energy(h, rho, u, xx.reshape(w.shape))
+
+    slope = (f(O.stiefel_step(x, g, eta)) - f(O.stiefel_step(x, g, -eta))) / (2 * eta)
+    assert slope == pytest.approx(-np.sum(r * r), rel=1e-6)
+
+
+def test_riemannian_sweeps_lower_the_energy():
+    """Small Riemannian steps: the energy per spin decreases sweep by sweep
+    (after the first few, while rho* settles) and stays above -4/pi."""
+    h1, shift = O.ising_h1(1.0)
+    layers = I.init_mera(0, 2)
+    rho = O.identity_density(2)
+    es = []
+    for _ in range(12):
+        layers, rho, e = O.sweep(layers, h1, shift, rho, 20, eta=0.1)
+        es.append(e)
+    assert all(b <= a + 1e-12 for a, b in zip(es[4:], es[5:]))
+    assert es[-1] >= -4.0 / np.pi

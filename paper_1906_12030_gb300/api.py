@@ -403,7 +403,9 @@ def mera_profile_read(kind: int = PROF_GEMM):
 
 
 def mera_device_status(clear: bool = True) -> int:
-    """Device failure bits (1 << 5: a bounded wait timed out); synchronises."""
+    """Device failure bits: 1 << MERA_ETIMEOUT (a bounded wait timed out),
+    1 << MERA_ENOTCONV (a polar update recorded in a graph did not converge).
+    Synchronises with the device."""
     st = ctypes.c_int(0)
     _check(library().mera_device_status(ctypes.byref(st), 1 if clear else 0))
     return st.value

@@ -76,6 +76,27 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(x: float, device) -> float:
+    """The largest x over all ranks of the default process group (x itself
+    without one).  `device`: where the reduction tensor lives (the rank's GPU
+    for NCCL, the CPU for gloo)."""
+    import torch
+
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return x
+    if torch.distributed.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_throughput(world: int, steps: int, max_ms: float) -> float:
+    """Whole-job sweeps per second: every rank runs `steps` sweeps of its own
+    replica, and the job takes as long as its slowest rank (max_ms)."""
+    return world * steps / (max_ms / 1e3)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -288,11 +309,7 @@ def run_native(args):
     sweep_flops = _sweep_flops(m, chi)
 
     def max_over_ranks(x):
-        if world > 1:
-            t = torch.tensor([x], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            return t.item()
-        return x
+        return _max_over_ranks(x, dev)
 
     # ---- direct calls (mera_sweep per step), with per-kernel timing -------
     launches0 = m.mera_launch_count()
@@ -318,7 +335,7 @@ def run_native(args):
     perm = m.mera_profile_read(m.PROF_PERMUTE)
     m.mera_profile_enable(False)
     energy = e.item()
-    direct = {"value": world * args.steps / (direct_ms / 1e3), "unit": "sweep/s",
+    direct = {"value": _job_throughput(world, args.steps, direct_ms), "unit": "sweep/s",
               "ms_per_step": direct_ms / args.steps, "gpu_launches": launches_direct, "clocks": clk_direct.summary(),
               "note": "one mera_sweep call per step; per-kernel CUDA events for the roofline and stage split"}
 
@@ -379,7 +396,7 @@ def run_native(args):
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms = max_over_ranks(ev0.elapsed_time(ev1))
-        e2e = {"value": world * n_e2e / (e2e_ms / 1e3), "unit": "sweep/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": _job_throughput(world, n_e2e, e2e_ms), "unit": "sweep/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 8, "steps": n_e2e,
                "path": "graph replay" if gr is not None else "mera_sweep"}
     if gr is not None:
@@ -407,7 +424,7 @@ def run_native(args):
         if world > 1:
             torch.distributed.destroy_process_group()
         return
-    value = world * args.steps / (total_ms / 1e3)
+    value = _job_throughput(world, args.steps, total_ms)
     if fp64 is not None:
         fp64["speedup_of_mixed"] = (value / world) / fp64["value"]
     peak, peak_src = _peak_tflops(args.prec)

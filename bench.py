@@ -56,6 +56,8 @@ def _args():
     ap.add_argument("--no-graph", action="store_true", help="skip the replayed-graph timing of the sweep")
     ap.add_argument("--sweeps", type=int, default=300, help="--case precision: optimisation sweeps per run")
     ap.add_argument("--polish", type=int, default=20, help="--case precision: FP64 sweeps after the mixed ones")
+    ap.add_argument("--z2", action="store_true",
+                    help="--case precision: start from Z2-symmetric tensors (kept by the sweep)")
     ap.add_argument("--riemannian-eta", type=float, default=0.0,
                     help="--case precision: also run --sweeps Riemannian-gradient sweeps with this step size")
     ap.add_argument("--grow-from", type=int, default=0,
@@ -636,7 +638,7 @@ def run_precision(args):
     S, P = args.sweeps, min(args.polish, args.sweeps)
 
     def fresh():
-        layers = I.init_mera(SEED, chi)
+        layers = I.init_mera(SEED, chi, z2=args.z2)
         us = [torch.from_numpy(u).to(dev).reshape(-1).contiguous() for u, _ in layers]
         ws_ = [torch.from_numpy(w).to(dev).contiguous() for _, w in layers]
         n3 = chi ** 3
@@ -684,7 +686,7 @@ def run_precision(args):
         m.mera_energy(h1, rho, us[0], ws_[0], cb, ct, e, prec=p)
         return 0.5 * (float(e.item()) + shift)
 
-    out = {"case": "precision", "chi": chi, "prec": args.prec, "sweeps": S, "polish_fp64_sweeps": P,
+    out = {"case": "precision", "chi": chi, "prec": args.prec, "sweeps": S, "polish_fp64_sweeps": P, "z2": args.z2,
            "exact_infinite_chain": -4.0 / np.pi}
     st, us, ws_, rho = fresh()
     hist_m, t_m = run(st, [prec] * S)
@@ -719,7 +721,7 @@ def run_precision(args):
     if args.grow_from > 0:
         from paper_1906_12030_gb300 import grow
 
-        layers0 = I.init_mera(SEED, args.grow_from)
+        layers0 = I.init_mera(SEED, args.grow_from, z2=args.z2)
         st0 = m.MeraState([torch.from_numpy(u).to(dev).reshape(-1).contiguous() for u, _ in layers0],
                           [torch.from_numpy(w).to(dev).contiguous() for _, w in layers0],
                           (torch.eye(args.grow_from ** 3, dtype=torch.float64, device=dev)

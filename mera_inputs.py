@@ -53,13 +53,46 @@ def random_u(rng: np.random.Generator, chi_b: int) -> np.ndarray:
     return random_isometry(rng, chi_b * chi_b, chi_b * chi_b).reshape(chi_b, chi_b, chi_b, chi_b)
 
 
-def init_mera(seed: int, chi: int, n_layers: int = 3, d: int = D_PHYS):
-    """Seeded initial tensors: list of (u, w) per layer, bottom layer first."""
+def parity_labels(dim: int, physical: bool = False) -> np.ndarray:
+    """Z2 charge of each basis state of a leg.  Physical (blocked) site:
+    index 2 s0 + s1 of two spins in the Z basis, charge = s0 xor s1 (the
+    parity prod Z of the transverse-field Ising chain).  Bond legs: the first
+    ceil(dim/2) states even, the rest odd."""
+    if physical:
+        return np.array([bin(i).count("1") % 2 for i in range(dim)])
+    return (np.arange(dim) >= (dim + 1) // 2).astype(int)
+
+
+def _block_isometry(rng, rows_p, cols_p, n_rows, n_cols):
+    """An n_rows x n_cols isometry that maps only rows of charge p to columns
+    of charge p (rows_p, cols_p: charge of each row / column)."""
+    q = np.zeros((n_rows, n_cols))
+    for p in (0, 1):
+        r = np.flatnonzero(rows_p == p)
+        c = np.flatnonzero(cols_p == p)
+        if len(c) == 0:
+            continue
+        q[np.ix_(r, c)] = random_isometry(rng, len(r), len(c))
+    return q
+
+
+def init_mera(seed: int, chi: int, n_layers: int = 3, d: int = D_PHYS, z2: bool = False):
+    """Seeded initial tensors: list of (u, w) per layer, bottom layer first.
+    z2: tensors that commute with the chain's Z2 parity (block-diagonal in
+    the charges of parity_labels), which the sweep then keeps."""
     rng = np.random.default_rng(seed)
     layers = []
+    pb = parity_labels(d, physical=True)
     for chi_b, chi_t in layer_dims(chi, n_layers, d):
-        u = random_u(rng, chi_b)
-        w = random_w(rng, chi_b, chi_t)
+        if not z2:
+            u = random_u(rng, chi_b)
+            w = random_w(rng, chi_b, chi_t)
+        else:
+            pt = parity_labels(chi_t)
+            pair = (pb[:, None] ^ pb[None, :]).reshape(-1)
+            u = _block_isometry(rng, pair, pair, chi_b * chi_b, chi_b * chi_b).reshape((chi_b,) * 4)
+            w = _block_isometry(rng, pair, pt, chi_b * chi_b, chi_t).reshape(chi_b, chi_b, chi_t)
+            pb = pt
         layers.append((u, w))
     return layers
 

@@ -388,3 +388,23 @@ def test_riemannian_sweeps_lower_the_energy():
         es.append(e)
     assert all(b <= a + 1e-12 for a, b in zip(es[4:], es[5:]))
     assert es[-1] >= -4.0 / np.pi
+
+
+def test_z2_symmetric_start_is_kept_by_the_sweep():
+    """Tensors that commute with the Ising chain's Z2 parity stay so under the
+    sweep (the Hamiltonian commutes with prod Z, so every environment is
+    block diagonal in the charges): the odd-charge blocks stay zero."""
+    chi = 4
+    layers = I.init_mera(1, chi, z2=True)
+    h1, shift = O.ising_h1(1.0)
+    layers, rho, _ = O.run(layers, 1.0, 3, 20)
+    pb = I.parity_labels(4, physical=True)
+    for u, w in layers:
+        cb, ct = w.shape[0], w.shape[2]
+        pt = I.parity_labels(ct)
+        pair = (pb[:, None] ^ pb[None, :]).reshape(-1)
+        W = w.reshape(cb * cb, ct)
+        U = u.reshape(cb * cb, cb * cb)
+        assert np.abs(W[pair[:, None] != pt[None, :]]).max() < 1e-12
+        assert np.abs(U[pair[:, None] != pair[None, :]]).max() < 1e-12
+        pb = pt

@@ -37,10 +37,24 @@ int tc_split_k(int prec, int64_t M, int64_t N, int64_t K) {
   const int64_t bk = 128 / elem_bytes(prec);  // K per stage of the GEMM kernel
   const int64_t num_k = (K + bk - 1) / bk;
   if (tiles >= kSMs || num_k < 8) return 1;
-  int64_t s = std::min<int64_t>((2 * kSMs + tiles - 1) / tiles, num_k / 4);
-  s = std::max<int64_t>(s, 1);
-  const int64_t kc = (num_k + s - 1) / s;
-  return int((num_k + kc - 1) / kc);  // every split non-empty
+  // At least two waves of work items; among the splits up to four times that
+  // (and at least 4 k-blocks per split) the one whose last wave is fullest,
+  // the smallest on ties.
+  const int64_t s_lo = std::max<int64_t>(1, std::min<int64_t>((2 * kSMs + tiles - 1) / tiles, num_k / 4));
+  const int64_t s_hi = std::max<int64_t>(s_lo, std::min<int64_t>(4 * s_lo, num_k / 4));
+  int64_t best = s_lo;
+  double best_eff = 0.0;
+  for (int64_t s = s_lo; s <= s_hi; ++s) {
+    const int64_t kc = (num_k + s - 1) / s;
+    const int64_t sn = (num_k + kc - 1) / kc;  // splits actually non-empty
+    const int64_t work = tiles * sn;
+    const double eff = double(work) / double(((work + kSMs - 1) / kSMs) * kSMs);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = sn;
+    }
+  }
+  return int(best);
 }
 
 int planes(int prec) { return prec == PREC_BF16X3 ? 2 : (prec == PREC_BF16X6 ? 3 : 1); }

@@ -170,7 +170,7 @@ def _emulate(plan, inputs, out_size, arena=None, reuse=False, keep=False):
     return (out, arena) if keep else out
 
 
-_SMALL = [(2, 2), (3, 3), (2, 3), (4, 3), (3, 5)]
+_SMALL = [(1, 1), (2, 1), (2, 2), (3, 3), (2, 3), (4, 3), (3, 5)]
 
 
 @pytest.mark.parametrize("prec,chi_b,chi_t",

@@ -17,7 +17,9 @@ m = pytest.importorskip("paper_1906_12030_gb300")
 pytestmark = pytest.mark.gpu
 
 TOL_F64 = 1e-10
-DIMS = [(2, 2), (3, 3), (4, 4), (5, 5), (2, 3), (4, 6), (4, 16), (3, 8), (8, 8)]
+# (1, 1) and (2, 1): the degenerate bond dimensions (every leg trivial, a
+# one-state coarse leg); the rest span several tiles with ragged edges.
+DIMS = [(1, 1), (2, 1), (2, 2), (3, 3), (4, 4), (5, 5), (2, 3), (4, 6), (4, 16), (3, 8), (8, 8)]
 
 
 def _cuda(x):

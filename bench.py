@@ -55,6 +55,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip the replayed-graph timing of the sweep")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the library's tile-width autotuner (run on the sweep's maps before timing)")
     ap.add_argument("--sweeps", type=int, default=300, help="--case precision: optimisation sweeps per run")
     ap.add_argument("--polish", type=int, default=20, help="--case precision: FP64 sweeps after the mixed ones")
     ap.add_argument("--z2", action="store_true",
@@ -98,6 +100,13 @@ def _job_throughput(world: int, steps: int, max_ms: float) -> float:
     """Whole-job sweeps per second: every rank runs `steps` sweeps of its own
     replica, and the job takes as long as its slowest rank (max_ms)."""
     return world * steps / (max_ms / 1e3)
+
+
+def _heuristic_bn(prec: str, n: int) -> int:
+    """The planner's tile width when nothing is tuned (for reporting)."""
+    if n > 128:
+        return 128 if prec == "bf16x6" else 256
+    return 128 if n > 64 else 64 if n > 16 else 16
 
 
 def _peaks():
@@ -302,6 +311,21 @@ def run_native(args):
 
         return us, ws_, rho, e, sweep
 
+    tuned = None
+    if not args.no_autotune and prec != m.PREC_F64:
+        # the library's tile-width autotuner, once, on every map of the sweep;
+        # record which chi^9-class steps it moved off the planner's width
+        n_shapes, moved = 0, set()
+        for cb, ct in I.layer_dims(chi):
+            for op in (m.OP_ASCEND, m.OP_DESCEND, m.OP_ENV_U, m.OP_ENV_W):
+                n_shapes += m.mera_autotune(op, cb, ct, prec, device=dev)
+        for cb, ct in I.layer_dims(chi):
+            for op in (m.OP_ASCEND, m.OP_DESCEND, m.OP_ENV_U, m.OP_ENV_W):
+                for dg in m.mera_plan_json(op, cb, ct, prec)["diagrams"]:
+                    for st in dg["steps"]:
+                        if st["kind"] == "gemm" and st["bn"] != _heuristic_bn(args.prec, st["N"]):
+                            moved.add((st["M"], st["N"], st["K"], st["bn"], bool(st["dominant"])))
+        tuned = {"shapes_timed": n_shapes, "moved": sorted(moved)}
     us, ws_, rho, e, sweep = make_state(prec)
     energies = []
     for _ in range(args.warmup):
@@ -455,6 +479,7 @@ def run_native(args):
         "stage_ms_per_step": {"gemm": allg[1] / args.steps, "gemm_dominant": dom[1] / args.steps,
                               "permute": perm[1] / args.steps},
         "gpu_launches": launches,
+        "autotune": tuned,
         "direct": direct,
         "clocks": clk.summary(),
         "e2e": e2e,

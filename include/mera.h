@@ -373,6 +373,26 @@ mera_status mera_ascend_noalloc(const double* h, const double* u, const double* 
                                 double* h_out, int prec, void* stream);
 
 /*
+ * Tile-width autotuner (batching/tuning extension; no counterpart in the
+ * paper).  Times every tensor-core GEMM step of op's program that has more
+ * than one sensible output-tile width (N > 64) and no K split, with each
+ * candidate width (256, 128, 64; 128 at most for MERA_PREC_BF16X6), on the
+ * program's own buffers in `ws` (ws_bytes >= mera_workspace_size(op, ...))
+ * and an output scratch of out_elems doubles (>= the op's output size); the
+ * contents of both are overwritten.  The fastest width (the planner's own
+ * choice unless another is at least 3 % faster) is recorded for the
+ * step's shape (mode, M, N, K, output format) and used by every program built
+ * afterwards (cached programs are discarded).  *n_tuned: shapes recorded.
+ * Results do not depend on the width beyond rounding (K-split counts may
+ * change with it).  mera_autotune_reset forgets all recorded widths.
+ * Synchronises with the device; call it when no call of this library is in
+ * flight.
+ */
+mera_status mera_autotune(int op, int chi_b, int chi_t, int prec, double* out_scratch, size_t out_elems, void* ws,
+                          size_t ws_bytes, void* stream, int* n_tuned);
+mera_status mera_autotune_reset(void);
+
+/*
  * Memory knob (no counterpart in the paper): a rank-7 intermediate of the
  * chi^9 contraction pairs larger than `bytes` (default 16 GiB) is computed
  * one slice at a time -- the pair runs once per value of one of its free

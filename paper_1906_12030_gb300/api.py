@@ -21,7 +21,7 @@ __all__ = [
     "workspace", "MeraState", "mera_launch_count", "mera_profile_enable", "mera_profile_read",
     "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE", "mera_device_status", "mera_gemm_test",
     "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_sweep_batch", "mera_set_slice_bytes", "MeraGraph", "mera_sweep_graph", "mera_stiefel_step",
-    "mera_stiefel_workspace_size", "mera_sweep_riemannian",
+    "mera_stiefel_workspace_size", "mera_sweep_riemannian", "mera_autotune", "mera_autotune_reset",
 ]
 
 PREC_F64, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3, 4
@@ -106,6 +106,8 @@ def library():
             "mera_stiefel_workspace_size": ([i, i, ctypes.POINTER(sz)], i),
             "mera_stiefel_step": ([vp, vp, i, i, d, vp, vp, sz, vp], i),
             "mera_sweep_riemannian": ([ctypes.POINTER(_State), vp, d, i, i, d, vp, sz, vp, vp], i),
+            "mera_autotune": ([i, i, i, i, vp, sz, vp, sz, vp, ctypes.POINTER(i)], i),
+            "mera_autotune_reset": ([], i),
             "mera_sweep_batch": ([ctypes.POINTER(_State), i, ctypes.POINTER(vp), ctypes.POINTER(d), i, i,
                                   ctypes.POINTER(vp), ctypes.POINTER(sz), vp, ctypes.POINTER(vp), i], i),
             "mera_profile_enable": ([i], i),
@@ -385,6 +387,26 @@ def mera_sweep_riemannian(state: MeraState, h1, shift, n_pow, eta, e_out, prec=P
     _check(library().mera_sweep_riemannian(ctypes.byref(st), _f64(h1, state.chi_b[0] ** 6, "h1"), float(shift), n_pow,
                                            prec, float(eta), p, n, _f64(e_out, 1, "e_out"), _stream(stream)))
     return e_out
+
+
+def mera_autotune(op: int, chi_b: int, chi_t: int, prec: int, device=None, stream=None) -> int:
+    """Time the tile widths of op's GEMM steps and record the fastest
+    (mera_autotune); returns the number of step shapes recorded."""
+    import torch
+
+    dev = device if device is not None else torch.device("cuda")
+    ws = workspace(mera_workspace_size(op, chi_b, chi_t, prec), dev)
+    n_out = {OP_ASCEND: chi_t ** 6, OP_DESCEND: chi_b ** 6, OP_ENV_U: chi_b ** 4, OP_ENV_W: chi_b ** 2 * chi_t}[op]
+    out = torch.empty(n_out, dtype=torch.float64, device=dev)
+    p, nb = _ws(ws)
+    n = ctypes.c_int(0)
+    _check(library().mera_autotune(op, chi_b, chi_t, prec, _f64(out, n_out, "out"), n_out, p, nb, _stream(stream),
+                                   ctypes.byref(n)))
+    return n.value
+
+
+def mera_autotune_reset() -> None:
+    _check(library().mera_autotune_reset())
 
 
 def mera_launch_count() -> int:

@@ -9,6 +9,7 @@
 #include <string>
 #include <atomic>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <vector>
 
@@ -197,6 +198,7 @@ mera_status run_program(const OpProgram& prog, const double* const inputs[4], do
         args.alpha = g.alpha;
         args.accumulate = g.accumulate;
         args.split = g.split;
+        args.bn = g.bn;
         args.partial = g.p_buf >= 0 ? reinterpret_cast<float*>(ws + dg.bufs[g.p_buf].offset) : nullptr;
         cudaError_t e = launch_gemm_tc(args, stream);
         if (e == cudaErrorNotSupported) return fail(MERA_EINVAL, "tensor-core GEMM unavailable for prec %d", prec);
@@ -906,6 +908,101 @@ extern "C" mera_status mera_sweep_batch(mera_state* states, int n, const double*
     }
   }
   return worst;
+}
+
+// Tile-width autotuner: every tensor-core GEMM step of the op's program that
+// has more than one sensible width (N > 64) and no K split is timed with each
+// width on the program's own buffers, and the fastest is recorded for that
+// step shape; later programs use it.
+extern "C" mera_status mera_autotune(int op, int chi_b, int chi_t, int prec, double* out_scratch,
+                                     size_t out_elems, void* ws, size_t ws_bytes, void* stream, int* n_tuned) {
+  if (!chi_ok(chi_b, chi_t)) return fail(MERA_EINVAL, "bad bond dimensions");
+  if (prec == PREC_F64 || !prec_ok(prec)) return fail(MERA_EINVAL, "autotuning needs a tensor-core mode");
+  if (op < OP_ASCEND || op > OP_ENV_W) return fail(MERA_EINVAL, "unknown op %d", op);
+  const OpProgram* prog = get_program(op, chi_b, chi_t, prec);
+  if (!prog) return fail(MERA_EINVAL, "no contraction program");
+  const size_t out_need = size_t(op == OP_ASCEND ? ipow(chi_t, 6)
+                                 : op == OP_DESCEND ? ipow(chi_b, 6)
+                                 : op == OP_ENV_U ? ipow(chi_b, 4) : ipow(chi_b, 2) * chi_t);
+  if (!out_scratch || out_elems < out_need) return fail(MERA_EINVAL, "output scratch too small");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(MERA_EINVAL, "workspace not 256-byte aligned");
+  if (!ws || ws_bytes < op_bytes(*prog)) return fail(MERA_ENOMEM, "workspace too small");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(ws);
+  struct Pick { int prec; int64_t M, N, K; int cf; int bn; };
+  std::vector<Pick> picks;
+  std::set<std::tuple<int64_t, int64_t, int64_t, int>> seen;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(MERA_ECUDA, "events");
+  mera_status st = MERA_OK;
+  for (const Program& dg : prog->diagrams) {
+    for (const Step& stp : dg.steps) {
+      if (stp.kind != 1) continue;
+      const GemmStep& g = stp.g;
+      const int cf = g.c_buf < 0 ? 1 : 0;
+      if (g.N <= 64 || g.split > 1 || !seen.insert({g.M, g.N, g.K, cf}).second) continue;
+      std::vector<int> cands = {128, 64};
+      if (g.N > 128 && prec != PREC_BF16X6) cands.insert(cands.begin(), 256);
+      if (g.N <= 128) cands = {128, 64};
+      // the planner's own choice wins unless another width is clearly (3 %)
+      // faster: single-step timings on scratch data carry noise
+      const int heur = tc_block_n(prec, g.N);
+      int best = 0;
+      float best_ms = 0.0f, heur_ms = 0.0f;
+      for (int bn : cands) {
+        if (tc_split_k(prec, g.M, g.N, g.K, bn) > 1) continue;  // timed only without a K split
+        TcGemmArgs a;
+        const int64_t eb = elem_bytes(prec);
+        a.prec = prec;
+        a.A = base + dg.bufs[g.a_buf].offset + g.a_off * eb;
+        a.a_plane_bytes = dg.bufs[g.a_buf].plane_bytes;
+        a.lda = g.lda;
+        a.B = base + dg.bufs[g.b_buf].offset + g.b_off * eb;
+        a.b_plane_bytes = dg.bufs[g.b_buf].plane_bytes;
+        a.ldb = g.ldb;
+        a.M = g.M; a.N = g.N; a.K = g.K;
+        a.c_final = cf != 0;
+        a.C = cf ? static_cast<void*>(out_scratch + g.c_off)
+                 : static_cast<void*>(base + dg.bufs[g.c_buf].offset + g.c_off * eb);
+        a.c_plane_elems = cf ? 0 : dg.bufs[g.c_buf].plane_bytes / eb;
+        a.m_dst = g.m_dst; a.n_dst = g.n_dst;
+        a.alpha = g.alpha; a.accumulate = 0;
+        a.split = 1; a.bn = bn;
+        cudaError_t e = launch_gemm_tc(a, s);  // warm
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = launch_gemm_tc(a, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+          st = cuda_status(e, "autotune launch");
+          break;
+        }
+        if (bn == heur) heur_ms = ms;
+        if (best == 0 || ms < best_ms) {
+          best = bn;
+          best_ms = ms;
+        }
+      }
+      if (st != MERA_OK) break;
+      if (best && heur_ms > 0.0f && best != heur && best_ms > 0.97f * heur_ms) best = heur;
+      if (best) picks.push_back({prec, g.M, g.N, g.K, cf, best});
+    }
+    if (st != MERA_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MERA_OK) return st;
+  for (const Pick& p : picks) set_tuned_tile(p.prec, p.M, p.N, p.K, p.cf, p.bn);
+  if (n_tuned) *n_tuned = int(picks.size());
+  return MERA_OK;
+}
+
+extern "C" mera_status mera_autotune_reset(void) {
+  clear_tuned_tiles();
+  return MERA_OK;
 }
 
 extern "C" mera_status mera_set_slice_bytes(size_t bytes) {

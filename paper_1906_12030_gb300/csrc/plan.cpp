@@ -29,10 +29,10 @@ int tc_block_n(int prec, int64_t N) {
   return 16;
 }
 
-int tc_split_k(int prec, int64_t M, int64_t N, int64_t K) {
+int tc_split_k(int prec, int64_t M, int64_t N, int64_t K, int bn_in) {
   if (prec == PREC_F64) return 1;
   constexpr int64_t kSMs = 152;
-  const int64_t bn = tc_block_n(prec, N);
+  const int64_t bn = bn_in > 0 ? bn_in : tc_block_n(prec, N);
   const int64_t tiles = ((M + 127) / 128) * ((N + bn - 1) / bn);
   const int64_t bk = 128 / elem_bytes(prec);  // K per stage of the GEMM kernel
   const int64_t num_k = (K + bk - 1) / bk;
@@ -364,7 +364,8 @@ struct Builder {
     gs.accumulate = (i == tr.root) ? accumulate : 0;
     gs.flops = 2.0 * double(gs.M) * double(gs.N) * double(gs.K);
     gs.dominant = full_flops_dominant_hint ? 2 : 0;  // resolved after emission
-    gs.split = tc_split_k(prec, gs.M, gs.N, gs.K);
+    gs.bn = prec == PREC_F64 ? 0 : tc_tile_n(prec, gs.M, gs.N, gs.K, i == tr.root ? 1 : 0);
+    gs.split = tc_split_k(prec, gs.M, gs.N, gs.K, gs.bn);
     if (gs.split > 1) {  // FP32 partials [split][N][M], live during this step only
       Buffer pb;
       pb.rows = int64_t(gs.split) * gs.N;
@@ -669,6 +670,8 @@ struct Key {
 std::mutex g_mu;
 std::map<Key, std::unique_ptr<OpProgram>> g_cache;
 size_t g_slice_bytes = size_t(16) << 30;  // 16 GiB
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int64_t, int64_t, int64_t, int>, int> g_tuned;  // (prec, M, N, K, c_final) -> width
 
 }  // namespace
 
@@ -768,6 +771,42 @@ const OpProgram* get_program(int op, int chi_b, int chi_t, int prec) {
   return out;
 }
 
+int tc_tile_n(int prec, int64_t M, int64_t N, int64_t K, int c_final) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(std::make_tuple(prec, M, N, K, c_final));
+    if (it != g_tuned.end()) return it->second;
+  }
+  return tc_block_n(prec, N);
+}
+
+void set_tuned_tile(int prec, int64_t M, int64_t N, int64_t K, int c_final, int bn) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const auto key = std::make_tuple(prec, M, N, K, c_final);
+    if (bn > 0)
+      g_tuned[key] = bn;
+    else
+      g_tuned.erase(key);
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_cache.clear();
+}
+
+void clear_tuned_tiles() {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_cache.clear();
+}
+
+int tuned_tile_count() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return int(g_tuned.size());
+}
+
 void set_slice_bytes(size_t bytes) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_slice_bytes = bytes;
@@ -818,7 +857,7 @@ std::string program_json(const OpProgram& prog, int op, int chi_b, int chi_t, in
           << ",\"c_buf\":" << g.c_buf << ",\"alpha\":" << g.alpha << ",\"accumulate\":" << g.accumulate
           << ",\"flops\":" << g.flops << ",\"dominant\":" << g.dominant << ",\"split\":" << g.split
           << ",\"p_buf\":" << g.p_buf << ",\"a_off\":" << g.a_off << ",\"b_off\":" << g.b_off
-          << ",\"c_off\":" << g.c_off << ",\"stat\":" << g.stat << ",\"m_dst\":";
+          << ",\"c_off\":" << g.c_off << ",\"stat\":" << g.stat << ",\"bn\":" << g.bn << ",\"m_dst\":";
         lm(g.m_dst);
         o << ",\"n_dst\":";
         lm(g.n_dst);

@@ -54,6 +54,7 @@ struct GemmStep {
   double flops = 0.0;
   int dominant = 0;   // one of the chi^9-class steps of its diagram
   int split = 1;      // K split over this many CTAs (tensor-core modes; partials summed in FP64)
+  int bn = 0;         // tensor-core tile width (16, 64, 128 or 256); 0 for the FP64 kernel
   int64_t a_off = 0, b_off = 0, c_off = 0;  // element offsets into A, B and the destination (slices)
   int p_buf = -1;     // FP32 partial-sum buffer [split][N][M] when split > 1
   int stat = 0;       // reads only u and w (directly or through such steps): its output is kept
@@ -102,7 +103,15 @@ int elem_bytes(int prec);   // storage bytes of one operand element (one plane)
 int tc_block_n(int prec, int64_t N);
 // K split of a tensor-core GEMM: > 1 when too few output tiles would leave
 // most SMs idle and K is long (each split keeps >= 4 k-blocks).
-int tc_split_k(int prec, int64_t M, int64_t N, int64_t K);
+int tc_split_k(int prec, int64_t M, int64_t N, int64_t K, int bn = 0);
+
+// Tile width of a tensor-core GEMM step: a width recorded by the autotuner
+// for this (prec, M, N, K, caller-format output) if any, else tc_block_n.
+int tc_tile_n(int prec, int64_t M, int64_t N, int64_t K, int c_final);
+// Records a tuned width (0 forgets it) and discards the cached programs.
+void set_tuned_tile(int prec, int64_t M, int64_t N, int64_t K, int c_final, int bn);
+void clear_tuned_tiles();
+int tuned_tile_count();
 int planes(int prec);       // 2 for BF16X3 (hi, lo), 3 for BF16X6 (hi, mid, lo), else 1
 
 // Builds (and caches) the program; thread safe.  Returns nullptr on bad input.

@@ -670,6 +670,16 @@ cudaError_t launch_cfg(const TcGemmArgs& a, cudaStream_t stream) {
 
 template <int PREC>
 cudaError_t launch_prec(const TcGemmArgs& a, cudaStream_t stream) {
+  switch (a.bn) {  // a width chosen by the planner (heuristic or autotuned)
+    case 0: break;
+    case 256:
+      if constexpr (PREC == PREC_BF16X6) return cudaErrorInvalidValue;  // one stage only
+      else return launch_cfg<PREC, 256>(a, stream);
+    case 128: return launch_cfg<PREC, 128>(a, stream);
+    case 64: return launch_cfg<PREC, 64>(a, stream);
+    case 16: return launch_cfg<PREC, 16>(a, stream);
+    default: return cudaErrorInvalidValue;
+  }
   // three-plane operands: a 256-wide B tile leaves room for one stage only
   if (a.N > 128 && PREC != PREC_BF16X6) return launch_cfg<PREC, (PREC == PREC_BF16X6 ? 128 : 256)>(a, stream);
   if (a.N > 64) return launch_cfg<PREC, 128>(a, stream);

@@ -29,6 +29,7 @@ struct TcGemmArgs {
   double alpha = 1.0;
   int accumulate = 0;
   int split = 1;             // K split (from tc_split_k); > 1 needs `partial`
+  int bn = 0;                // tile width 16/64/128/256; 0: chosen from N
   float* partial = nullptr;  // FP32 scratch [split][N][M]
 };
 

@@ -347,3 +347,17 @@ def test_rerun_with_kept_uw_products(prec, chi):
     for got, rho in ((out1, r1), (out2, r2)):
         want = O.descend(rho, u, w).reshape(-1)
         assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
+
+
+def test_plans_carry_tile_widths():
+    """Tensor-core steps carry the tile width the kernel will use (from N when
+    nothing is tuned); FP64 steps carry none."""
+    m.mera_autotune_reset()
+    plan = m.mera_plan_json(m.OP_ASCEND, 16, 16, m.PREC_BF16X3)
+    for dg in plan["diagrams"]:
+        for st in dg["steps"]:
+            if st["kind"] == "gemm":
+                want = 256 if st["N"] > 128 else 128 if st["N"] > 64 else 64 if st["N"] > 16 else 16
+                assert st["bn"] == want
+    plan = m.mera_plan_json(m.OP_ASCEND, 4, 4, m.PREC_F64)
+    assert all(st["bn"] == 0 for dg in plan["diagrams"] for st in dg["steps"] if st["kind"] == "gemm")

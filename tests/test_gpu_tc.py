@@ -242,3 +242,23 @@ def test_full_size_properties(chi):
     tr_out = float(out.reshape(n3, n3).diagonal().sum())
     assert abs(tr_out - tr_in) <= MAP_TOL[prec] * float(rho.reshape(n3, n3).diagonal().abs().sum()) + 1e-9
     torch.cuda.synchronize()
+
+
+def test_autotuned_widths_keep_the_maps():
+    """The tile-width autotuner records a width for the large GEMM shapes of
+    the chi = 8 programs; the maps built afterwards use those widths (the
+    plan says so) and still match the oracle within the mode's tolerance."""
+    prec, chi = m.PREC_BF16X3, 8
+    m.mera_autotune_reset()
+    try:
+        n = m.mera_autotune(m.OP_ASCEND, chi, chi, prec) + m.mera_autotune(m.OP_ENV_W, chi, chi, prec)
+        assert n > 0
+        widths = {st["bn"] for dg in m.mera_plan_json(m.OP_ENV_W, chi, chi, prec)["diagrams"]
+                  for st in dg["steps"] if st["kind"] == "gemm"}
+        assert widths <= {16, 64, 128, 256}
+        res = _maps(prec, chi, chi, 21)
+        for name, (got, want) in res.items():
+            g = got.cpu().numpy().reshape(want.shape)
+            assert np.abs(g - want).max() / np.abs(want).max() < MAP_TOL[prec], name
+    finally:
+        m.mera_autotune_reset()

@@ -55,6 +55,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip the replayed-graph timing of the sweep")
+    ap.add_argument("--tune", action="store_true", help="--case ascend|descend|env_u|env_w: autotune the map first")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the library's tile-width autotuner (run on the sweep's maps before timing)")
     ap.add_argument("--sweeps", type=int, default=300, help="--case precision: optimisation sweeps per run")
@@ -541,13 +542,18 @@ def run_case(args):
         else:
             m.mera_env_w(hd, rd, ud, wd, chi, chi, out[: chi ** 3], prec=prec, ws=ws)
 
+    if args.tune:
+        m.mera_autotune(op, chi, chi, prec)
+        ws = m.workspace(m.mera_workspace_size(op, chi, chi, prec))
     call()
     torch.cuda.synchronize()
     m.mera_profile_enable(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")  # ncu --nvtx --nvtx-include "timed/" selects this call
     e0.record()
     call()
     e1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     dom, allg, perm = (m.mera_profile_read(k) for k in (m.PROF_GEMM_DOMINANT, m.PROF_GEMM, m.PROF_PERMUTE))

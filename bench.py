@@ -127,7 +127,7 @@ def _peak_tflops(prec: str):
 # DRAM bytes per launch of the chi^9-class GEMMs, from the ncu capture named
 # here (profiles/).  Reported only for the workload it was taken on; it must
 # be retaken (or set to None) whenever the kernel changes.
-ROOFLINE_TRAFFIC = {("bf16x3", 16): (1.121e9, "profiles/tc_gemm_bf16x3_chi16_ascend.md")}
+ROOFLINE_TRAFFIC = {("bf16x3", 16): (1.128e9, "profiles/tc_gemm_bf16x3_chi16_ascend.md (autotuned widths)")}
 
 
 def _sweep_flops(m, chi):

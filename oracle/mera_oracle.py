@@ -27,6 +27,13 @@ reading fixed from its text, equations and contribution counts:
   dE/dw = 2 Gamma_w and dE/du = 2 Gamma_u.
 * Fig. 5 and Sec. II C: the update is -U V^T from the SVD of the environment
   (lower legs as rows, upper legs as columns).
+* stiefel_step / sweep(eta=...): a Riemannian gradient step on the Stiefel
+  manifold, an alternative update (not the paper's), pinned by tangency, the
+  retraction and its first-order decrease of the energy.
+
+Parity unpinned: the Ising-CFT scaling dimensions (1/8, 1, 9/8) are not
+reached by optimisations the oracle can run, so they pin nothing here (the
+dimensions of the identity, 0, and of exactly solvable cases are pinned).
 """
 from __future__ import annotations
 

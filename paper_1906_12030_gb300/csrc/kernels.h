@@ -69,7 +69,6 @@ cudaError_t launch_stiefel_combine(const double* X, const double* G, const doubl
 // Sets the conditional handle of a recorded while loop to (state[0] == 0 and
 // state[1] < max_iter).
 cudaError_t launch_ns_continue(const int* state, cudaGraphConditionalHandle h, int max_iter, cudaStream_t stream);
-cudaError_t launch_scale_copy(const double* src, double* dst, int64_t count, double alpha,
-                              cudaStream_t stream);
+
 
 }  // namespace mera

@@ -631,11 +631,6 @@ cudaError_t launch_ns_finish(int* state, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) scale_copy_kernel(const double* __restrict__ src, double* dst, int64_t count,
-                                                         double alpha) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x)
-    dst[i] = alpha * src[i];
-}
 
 // out = -X with X the iterate the Newton-Schulz state points at (buffer
 // state[1] & 1), chosen on the device so that no host read is needed.  The
@@ -701,12 +696,5 @@ cudaError_t launch_ns_continue(const int* state, cudaGraphConditionalHandle h, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_scale_copy(const double* src, double* dst, int64_t count, double alpha, cudaStream_t stream) {
-  const int nb = int(std::min<int64_t>((count + 255) / 256, 1024));
-  if (nb <= 0) return cudaSuccess;
-  count_launch();
-  scale_copy_kernel<<<nb, 256, 0, stream>>>(src, dst, count, alpha);
-  return cudaGetLastError();
-}
 
 }  // namespace mera

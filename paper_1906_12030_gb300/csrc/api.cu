@@ -1,6 +1,8 @@
 // C ABI of the MERA library: argument checks, contraction-program execution,
-// the scale-invariant fixed point, the polar update, the energy and the
-// native sweep driver.
+// the scale-invariant fixed point, the polar update (Newton-Schulz; a
+// conditional while loop when recorded into a graph), the Stiefel gradient
+// step, the energy, the native sweep driver (SVD or Riemannian updates),
+// batched sweeps, recorded sweep graphs and the tile-width autotuner.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>

@@ -480,6 +480,9 @@ def run_native(args):
         "stage_ms_per_step": {"gemm": allg[1] / args.steps, "gemm_dominant": dom[1] / args.steps,
                               "permute": perm[1] / args.steps},
         "gpu_launches": launches,
+        "gpu_launches_counting": ("kernel nodes of the recorded sweep per replay; the body of each polar update's "
+                                  "while loop counts once although it runs several times") if graph_ms is not None
+        else "kernel launches issued by the library",
         "autotune": tuned,
         "direct": direct,
         "clocks": clk.summary(),

@@ -53,7 +53,7 @@ struct GemmStep {
   int accumulate = 0;
   double flops = 0.0;
   int dominant = 0;   // one of the chi^9-class steps of its diagram
-  int split = 1;      // K split over this many CTAs (tensor-core modes; partials summed in FP64)
+  int split = 1;      // K split over this many CTAs (tensor-core modes; partials summed by a TwoSum pair)
   int bn = 0;         // tensor-core tile width (16, 64, 128 or 256); 0 for the FP64 kernel
   int64_t a_off = 0, b_off = 0, c_off = 0;  // element offsets into A, B and the destination (slices)
   int p_buf = -1;     // FP32 partial-sum buffer [split][N][M] when split > 1

@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (lane == 0) mbar_arrive(&acc_empty[b]);
         }
         if (!row_ok) continue;
-        if (ep.split > 1) {  // raw partial sums, reduced in FP64 afterwards
+        if (ep.split > 1) {  // raw partial sums, reduced afterwards (splitk_reduce_kernel)
           float* p = ep.partial + (ks * ep.N + n0 + c0) * ep.M + m;
 #pragma unroll
           for (int j = 0; j < 32; ++j, p += ep.M)

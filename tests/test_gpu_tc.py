@@ -262,3 +262,37 @@ def test_autotuned_widths_keep_the_maps():
             assert np.abs(g - want).max() / np.abs(want).max() < MAP_TOL[prec], name
     finally:
         m.mera_autotune_reset()
+
+
+def test_autotuned_widths_are_bit_identical_at_full_size():
+    """chi = 16, the benchmarked size: the widths the autotuner picks change
+    the tiling, not the order in which each output element sums its K range
+    (no step gains a K split here), so the maps come out bit for bit the same
+    as with the planner's widths."""
+    prec, chi = m.PREC_BF16X3, 16
+    rng = np.random.default_rng(16)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    ud, wd = _cuda(u).reshape(-1), _cuda(w).reshape(-1)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    h = torch.randn(chi ** 6, dtype=torch.float64, device="cuda", generator=g)
+    m.mera_autotune_reset()
+    try:
+        a0 = torch.empty_like(h)
+        d0 = torch.empty_like(h)
+        m.mera_ascend(h, ud, wd, chi, chi, a0, prec=prec)
+        m.mera_descend(h, ud, wd, chi, chi, d0, prec=prec)
+        m.mera_autotune(m.OP_ASCEND, chi, chi, prec)
+        m.mera_autotune(m.OP_DESCEND, chi, chi, prec)
+        split_steps = [st for op in (m.OP_ASCEND, m.OP_DESCEND) for dg in m.mera_plan_json(op, chi, chi, prec)["diagrams"]
+                 for st in dg["steps"] if st["kind"] == "gemm" and st["split"] > 1]
+        a1 = torch.empty_like(h)
+        d1 = torch.empty_like(h)
+        m.mera_ascend(h, ud, wd, chi, chi, a1, prec=prec)
+        m.mera_descend(h, ud, wd, chi, chi, d1, prec=prec)
+        if not split_steps:
+            assert torch.equal(a0, a1) and torch.equal(d0, d1)
+        else:
+            assert float((a0 - a1).abs().max()) <= MAP_TOL[prec] * float(a0.abs().max())
+    finally:
+        m.mera_autotune_reset()

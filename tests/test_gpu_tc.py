@@ -284,8 +284,9 @@ def test_autotuned_widths_are_bit_identical_at_full_size():
         m.mera_descend(h, ud, wd, chi, chi, d0, prec=prec)
         m.mera_autotune(m.OP_ASCEND, chi, chi, prec)
         m.mera_autotune(m.OP_DESCEND, chi, chi, prec)
-        split_steps = [st for op in (m.OP_ASCEND, m.OP_DESCEND) for dg in m.mera_plan_json(op, chi, chi, prec)["diagrams"]
-                 for st in dg["steps"] if st["kind"] == "gemm" and st["split"] > 1]
+        plans = [m.mera_plan_json(op, chi, chi, prec) for op in (m.OP_ASCEND, m.OP_DESCEND)]
+        split_steps = [st for p in plans for dg in p["diagrams"] for st in dg["steps"]
+                       if st["kind"] == "gemm" and st["split"] > 1]
         a1 = torch.empty_like(h)
         d1 = torch.empty_like(h)
         m.mera_ascend(h, ud, wd, chi, chi, a1, prec=prec)

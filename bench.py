@@ -67,6 +67,8 @@ def _args():
     ap.add_argument("--grow-from", type=int, default=0,
                     help="--case precision: also optimise at this smaller chi first, grow, then --sweeps at --chi")
     ap.add_argument("--grow-sweeps", type=int, default=2000, help="--case precision: sweeps before growing")
+    ap.add_argument("--batch-chis", default="8,12,16",
+                    help="--case batch: bond dimensions the 32 MERAs draw from (8,12,16,20,24,32 for the full mix)")
     ap.add_argument("--scaling-k", type=int, default=0,
                     help="--case precision: also compare this many scaling dimensions (mixed vs FP64)")
     ap.add_argument("--case", default="sweep",
@@ -568,8 +570,12 @@ def run_case(args):
 
 
 def run_batch(args):
-    """Batching: 32 independent MERAs, h ~ U[0.9, 1.1], chi from {8, 12, 16}
-    (seeded), one sweep each per step; one-at-a-time vs mera_sweep_batch."""
+    """Batching: 32 independent MERAs, h ~ U[0.9, 1.1], chi drawn (seeded) from
+    --batch-chis, one sweep each per step.  Modes: one at a time (one shared
+    scratch), mera_sweep_batch over lanes (mera_batch_lanes: one scratch and
+    one stream per lane, under a budget of the device memory left after the
+    states), and one recorded sweep graph per MERA replayed on its lane's
+    stream."""
     import numpy as np
     import torch
 
@@ -577,8 +583,9 @@ def run_batch(args):
     import paper_1906_12030_gb300 as m
 
     prec = m.PRECS[args.prec]
+    pool = [int(c) for c in args.batch_chis.split(",")]
     rng = np.random.default_rng(SEED)
-    specs = [(s, int(rng.choice([8, 12, 16])), float(rng.uniform(0.9, 1.1))) for s in range(32)]
+    specs = [(s, int(rng.choice(pool)), float(rng.uniform(0.9, 1.1))) for s in range(32)]
 
     def make():
         out = []
@@ -588,41 +595,48 @@ def run_batch(args):
             ws_ = [torch.from_numpy(w).cuda().contiguous() for _, w in layers]
             rho = (torch.eye(chi ** 3, dtype=torch.float64, device="cuda") / chi ** 3).reshape(-1).contiguous()
             h1, shift = m.mera_ising_h1(hz)
-            st = m.MeraState(us, ws_, rho)
-            wsb = m.workspace(m.mera_sweep_workspace_size(st.chi_b, st.chi_t, prec))
-            out.append((st, torch.from_numpy(h1.reshape(-1)).cuda(), shift, wsb))
+            out.append((m.MeraState(us, ws_, rho), torch.from_numpy(h1.reshape(-1)).cuda(), shift))
         return out
 
     flops = sum(_sweep_flops(m, chi) for _, chi, _ in specs)
     res = {}
+    n_lanes = 0
     for mode in ("one_at_a_time", "batched", "graphs"):
         ms = make()
+        states = [x[0] for x in ms]
         e = torch.empty(len(ms), dtype=torch.float64, device="cuda")
-        streams = [torch.cuda.Stream() for _ in ms]
+        torch.cuda.synchronize()
+        if mode == "one_at_a_time":
+            shared = m.workspace(max(m.mera_sweep_workspace_size(st.chi_b, st.chi_t, prec) for st in states))
+        else:
+            free, _ = torch.cuda.mem_get_info()
+            wss, streams = m.batch_resources(states, prec, budget_bytes=int(0.9 * free), n_pow=N_POW)
+            n_lanes = len({id(x) for x in streams})
         graphs = []
-        if mode == "graphs":  # one recorded sweep per MERA, replayed on its own stream
-            for i, (st, h1, shift, wsb) in enumerate(ms):
-                graphs.append(m.mera_sweep_graph(st, h1, shift, N_POW, e[i:i + 1], prec=prec, ws=wsb,
+        if mode == "graphs":  # one recorded sweep per MERA, replayed on its lane's stream
+            for i, (st, h1, shift) in enumerate(ms):
+                graphs.append(m.mera_sweep_graph(st, h1, shift, N_POW, e[i:i + 1], prec=prec, ws=wss[i],
                                                  stream=streams[i]))
 
         def step():
             if mode == "graphs":
                 cur = torch.cuda.current_stream()
-                for g, sm in zip(graphs, streams):
+                for sm in streams:
                     sm.wait_stream(cur)
+                for g, sm in zip(graphs, streams):
                     g.launch(sm)
                 for sm in streams:
                     cur.wait_stream(sm)
             elif mode == "batched":
                 try:
-                    m.mera_sweep_batch([x[0] for x in ms], [x[1] for x in ms], [x[2] for x in ms], N_POW, e,
-                                       prec=prec, wss=[x[3] for x in ms], streams=streams, n_threads=16)
+                    m.mera_sweep_batch(states, [x[1] for x in ms], [x[2] for x in ms], N_POW, e, prec=prec,
+                                       wss=wss, streams=streams, n_threads=16)
                 except m.MeraNotConverged:
                     pass
             else:
-                for i, (st, h1, shift, wsb) in enumerate(ms):
+                for i, (st, h1, shift) in enumerate(ms):
                     try:
-                        m.mera_sweep(st, h1, shift, N_POW, e[i:i + 1], prec=prec, ws=wsb)
+                        m.mera_sweep(st, h1, shift, N_POW, e[i:i + 1], prec=prec, ws=shared)
                     except m.MeraNotConverged:
                         pass
 
@@ -638,15 +652,18 @@ def run_batch(args):
                      "energies": e.cpu().tolist()}
         for g in graphs:
             g.close()
-        del ms
+        del ms, states, e
+        shared = wss = streams = None
+        torch.cuda.empty_cache()
     same = (res["batched"]["energies"] == res["one_at_a_time"]["energies"]
             and res["graphs"]["energies"] == res["one_at_a_time"]["energies"])
     for r in res.values():
         r.pop("energies")
     base = res["one_at_a_time"]["mera_sweeps_per_s"]
     print(json.dumps({"case": "batch", "prec": args.prec, "n_meras": len(specs),
-                      "chis": [c for _, c, _ in specs], "steps": args.steps, "warmup": args.warmup,
-                      "results": res, "speedup": res["batched"]["mera_sweeps_per_s"] / base,
+                      "chis": [c for _, c, _ in specs], "n_lanes": n_lanes, "steps": args.steps,
+                      "warmup": args.warmup, "results": res,
+                      "speedup": res["batched"]["mera_sweeps_per_s"] / base,
                       "speedup_graphs": res["graphs"]["mera_sweeps_per_s"] / base,
                       "identical_energies": same}), flush=True)
 

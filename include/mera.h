@@ -220,16 +220,39 @@ mera_status mera_sweep(mera_state* state, const double* h1_dev, double shift, in
  * dimensions and precision-independent state): states[i] with h1[i]
  * (device, [chi_b[0]^6]) and shift[i], scratch ws[i] of ws_bytes[i]
  * (mera_sweep_workspace_size of that state), energy written to e_dev[i]
- * (device), work issued on streams[i].  The sweeps run concurrently: a pool
- * of n_threads host threads issues them, so that one MERA's host-side
- * convergence checks do not hold back the others.  Each MERA's result is
- * exactly what mera_sweep gives for it alone.  Returns the most severe
- * status of the batch (MERA_ENOTCONV if only polar caps were hit); the
- * error text names the MERA.  Streams and scratch must be distinct per MERA.
+ * (device), work issued on streams[i].  MERAs that share a stream form a
+ * lane: one host thread issues its members in index order, so they run one
+ * after another and may share one scratch buffer (large enough for each of
+ * them).  Lanes run concurrently: a pool of n_threads host threads issues
+ * them, so that one MERA's host-side convergence checks do not hold back the
+ * others.  Each MERA's result is exactly what mera_sweep gives for it alone.
+ * Returns the most severe status of the batch (MERA_ENOTCONV if only polar
+ * caps were hit); the error text names the MERA.  MERA_EINVAL, before any
+ * work, if one scratch pointer is given with two different streams (only
+ * identical pointers are detected; partly overlapping buffers are the
+ * caller's error).
  */
 mera_status mera_sweep_batch(mera_state* states, int n, const double* const* h1, const double* shift,
                              int n_pow, int prec, void* const* ws, const size_t* ws_bytes, double* e_dev,
                              void* const* streams, int n_threads);
+
+/*
+ * Lanes for mera_sweep_batch under a device-memory budget (host only, no
+ * device access).  MERA i has n_layers layers with dimensions
+ * chi_b[i * n_layers + k], chi_t[i * n_layers + k]; its scratch is
+ * mera_sweep_workspace_size and its cost the contraction flops of one sweep
+ * with n_pow power steps.  Longest-processing-time-first list scheduling:
+ * MERAs are taken by decreasing scratch (then cost); each opens a new lane
+ * while fewer than max_lanes exist and its scratch fits in what is left of
+ * budget_bytes, otherwise it joins the lane with the least cost so far.
+ * Outputs: lane[i] in [0, *n_lanes) for every MERA, and lane_bytes[l] (room
+ * for n entries) the scratch of lane l, which covers each of its members;
+ * the lane_bytes sum to at most budget_bytes.  MERA_ENOMEM if the largest
+ * MERA alone exceeds the budget; MERA_EINVAL for bad dimensions (the error
+ * text names the MERA) or arguments.
+ */
+mera_status mera_batch_lanes(int n, int n_layers, const int* chi_b, const int* chi_t, int prec, int n_pow,
+                             size_t budget_bytes, int max_lanes, int* lane, int* n_lanes, size_t* lane_bytes);
 
 /*
  * Riemannian alternative to the polar update (the paper notes gradients can be

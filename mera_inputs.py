@@ -113,3 +113,23 @@ def random_density(rng: np.random.Generator, chi: int) -> np.ndarray:
     r = g @ g.T
     r /= np.trace(r)
     return r.reshape((chi,) * 6)
+
+
+def random_diagonal_density(rng: np.random.Generator, chi: int) -> np.ndarray:
+    """A random full-rank diagonal 3-site density matrix (entries U[0.5, 1.5],
+    normalised to unit trace)."""
+    n = chi ** 3
+    d = rng.uniform(0.5, 1.5, n)
+    r = np.zeros((n, n))
+    r[np.arange(n), np.arange(n)] = d / d.sum()
+    return r.reshape((chi,) * 6)
+
+
+def random_low_rank_density(rng: np.random.Generator, chi: int, rank: int) -> np.ndarray:
+    """A random 3-site density matrix of the given rank (V V^T / tr): cheap to
+    draw at large chi, where a full-rank Gram matrix costs chi^9."""
+    n = chi ** 3
+    v = rng.standard_normal((n, rank))
+    r = v @ v.T
+    r /= np.trace(r)
+    return r.reshape((chi,) * 6)

@@ -22,6 +22,7 @@ __all__ = [
     "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE", "mera_device_status", "mera_gemm_test",
     "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_sweep_batch", "mera_set_slice_bytes", "MeraGraph", "mera_sweep_graph", "mera_stiefel_step",
     "mera_stiefel_workspace_size", "mera_sweep_riemannian", "mera_autotune", "mera_autotune_reset",
+    "mera_batch_lanes", "batch_resources",
 ]
 
 PREC_F64, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3, 4
@@ -110,6 +111,8 @@ def library():
             "mera_autotune_reset": ([], i),
             "mera_sweep_batch": ([ctypes.POINTER(_State), i, ctypes.POINTER(vp), ctypes.POINTER(d), i, i,
                                   ctypes.POINTER(vp), ctypes.POINTER(sz), vp, ctypes.POINTER(vp), i], i),
+            "mera_batch_lanes": ([i, i, ctypes.POINTER(i), ctypes.POINTER(i), i, i, sz, i, ctypes.POINTER(i),
+                                  ctypes.POINTER(i), psz], i),
             "mera_profile_enable": ([i], i),
             "mera_profile_read": ([i, ctypes.POINTER(ctypes.c_longlong), pd, pd], i),
         }
@@ -471,7 +474,9 @@ def mera_sweep_batch(states, h1s, shifts, n_pow, e_out, prec=PREC_F64, wss=None,
 
     states: list of MeraState; h1s: device h1 per MERA; shifts: floats;
     e_out: device float64 tensor with one slot per MERA; wss: scratch per
-    MERA (allocated when None); streams: one torch.cuda.Stream per MERA."""
+    MERA (allocated when None); streams: a torch.cuda.Stream per MERA.  MERAs
+    given the same stream run one after another and may share scratch
+    (batch_resources makes such lanes under a memory budget)."""
     import torch
 
     n = len(states)
@@ -494,6 +499,38 @@ def mera_sweep_batch(states, h1s, shifts, n_pow, e_out, prec=PREC_F64, wss=None,
     for s in streams:
         cur.wait_stream(s)
     return e_out
+
+
+def mera_batch_lanes(dims, prec, budget_bytes, max_lanes=32, n_pow=20):
+    """Lanes of a batch under a scratch budget (mera_batch_lanes).
+
+    dims: one (chi_b list, chi_t list) per MERA, all with the same number of
+    layers.  Returns (lane of each MERA, scratch bytes of each lane)."""
+    n = len(dims)
+    n_layers = len(dims[0][0])
+    if any(len(b) != n_layers or len(t) != n_layers for b, t in dims):
+        raise ValueError("every MERA of a batch needs the same number of layers")
+    cb = (ctypes.c_int * (n * n_layers))(*[x for b, _ in dims for x in b])
+    ct = (ctypes.c_int * (n * n_layers))(*[x for _, t in dims for x in t])
+    lane = (ctypes.c_int * n)()
+    lane_bytes = (ctypes.c_size_t * n)()
+    n_lanes = ctypes.c_int(0)
+    _check(library().mera_batch_lanes(n, n_layers, cb, ct, prec, n_pow, int(budget_bytes), max_lanes, lane,
+                                      ctypes.byref(n_lanes), lane_bytes))
+    return list(lane), [int(lane_bytes[k]) for k in range(n_lanes.value)]
+
+
+def batch_resources(states, prec, budget_bytes, max_lanes=32, n_pow=20, device=None):
+    """Scratch and streams for mera_sweep_batch under a memory budget: one
+    buffer and one stream per lane of mera_batch_lanes, shared by the lane's
+    MERAs.  Returns (wss, streams), one entry per MERA."""
+    import torch
+
+    dev = device if device is not None else torch.device("cuda")
+    lanes, lane_bytes = mera_batch_lanes([(s.chi_b, s.chi_t) for s in states], prec, budget_bytes, max_lanes, n_pow)
+    bufs = [workspace(b, dev) for b in lane_bytes]
+    strs = [torch.cuda.Stream(device=dev) for _ in lane_bytes]
+    return [bufs[k] for k in lanes], [strs[k] for k in lanes]
 
 
 def mera_set_slice_bytes(nbytes: int) -> None:

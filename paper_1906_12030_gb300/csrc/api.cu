@@ -10,6 +10,7 @@
 #include <cstring>
 #include <string>
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <set>
 #include <thread>
@@ -884,18 +885,33 @@ extern "C" mera_status mera_sweep_batch(mera_state* states, int n, const double*
                                         void* const* streams, int n_threads) {
   if (!states || n < 1 || !h1 || !shift || !ws || !ws_bytes || !e_dev || !streams)
     return fail(MERA_EINVAL, "null argument to mera_sweep_batch");
-  if (n_threads < 1) n_threads = 1;
-  n_threads = std::min(n_threads, n);
+  // MERAs on one stream form a group that one host thread issues in index
+  // order, so its members run one after another and may share scratch;
+  // scratch handed to two streams would be written by concurrent sweeps.
+  std::vector<std::vector<int>> groups;
+  std::map<void*, size_t> group_of;
+  std::map<void*, void*> stream_of_ws;
+  for (int i = 0; i < n; ++i) {
+    auto w = stream_of_ws.emplace(ws[i], streams[i]);
+    if (!w.second && w.first->second != streams[i])
+      return fail(MERA_EINVAL, "MERA %d: its scratch is also used on another stream", i);
+    auto g = group_of.emplace(streams[i], groups.size());
+    if (g.second) groups.emplace_back();
+    groups[g.first->second].push_back(i);
+  }
+  n_threads = std::max(1, std::min(n_threads, int(groups.size())));
   std::vector<mera_status> st(static_cast<size_t>(n), MERA_OK);
   std::vector<std::string> msg(static_cast<size_t>(n));
   int dev = 0;
   cudaGetDevice(&dev);
   auto worker = [&](int t) {
     cudaSetDevice(dev);  // host threads start on device 0
-    for (int i = t; i < n; i += n_threads) {
-      st[size_t(i)] = mera_sweep(&states[i], h1[i], shift[i], n_pow, prec, ws[i], ws_bytes[i], e_dev + i, streams[i]);
-      if (st[size_t(i)] != MERA_OK) msg[size_t(i)] = g_err;
-    }
+    for (size_t g = size_t(t); g < groups.size(); g += size_t(n_threads))
+      for (int i : groups[g]) {
+        st[size_t(i)] = mera_sweep(&states[i], h1[i], shift[i], n_pow, prec, ws[i], ws_bytes[i], e_dev + i,
+                                   streams[i]);
+        if (st[size_t(i)] != MERA_OK) msg[size_t(i)] = g_err;
+      }
   };
   std::vector<std::thread> pool;
   for (int t = 1; t < n_threads; ++t) pool.emplace_back(worker, t);
@@ -910,6 +926,81 @@ extern "C" mera_status mera_sweep_batch(mera_state* states, int n, const double*
     }
   }
   return worst;
+}
+
+// Contraction flops of one sweep (the stages of sweep_impl): per transitional
+// layer an ascent of h, both environments, and a descent of rho (the bottom
+// layer's last map is the energy, an ascent's network); the scale-invariant
+// layer adds n_pow descents for rho*.
+static double sweep_flops(int n, const int* cb, const int* ct, int n_pow) {
+  double tot = 0.0;
+  for (int k = 0; k < n; ++k) {
+    double f[4] = {0, 0, 0, 0};
+    for (int op = OP_ASCEND; op <= OP_ENV_W; ++op) {
+      const OpProgram* p = get_program(op, cb[k], ct[k], MERA_PREC_F64);
+      f[op] = p ? p->flops : 0.0;
+    }
+    tot += f[OP_ENV_U] + f[OP_ENV_W];
+    if (k + 1 < n) tot += f[OP_ASCEND] + (k == 0 ? f[OP_ASCEND] : f[OP_DESCEND]);
+    else tot += double(n_pow) * f[OP_DESCEND];
+  }
+  return tot;
+}
+
+// Lanes of a batch: longest-processing-time-first list scheduling under a cap
+// on the summed scratch.  MERAs are taken by decreasing scratch size (then
+// cost); each opens a lane while lanes and budget remain, else joins the
+// least-loaded lane, whose scratch (sized by its first, largest member)
+// already holds it.
+extern "C" mera_status mera_batch_lanes(int n, int n_layers, const int* chi_b, const int* chi_t, int prec, int n_pow,
+                                        size_t budget_bytes, int max_lanes, int* lane, int* n_lanes,
+                                        size_t* lane_bytes) {
+  if (n < 1 || n_layers < 1 || n_layers > MERA_MAX_LAYERS || !chi_b || !chi_t || n_pow < 0 || max_lanes < 1 ||
+      !lane || !n_lanes || !lane_bytes)
+    return fail(MERA_EINVAL, "bad arguments to mera_batch_lanes");
+  std::vector<size_t> need(static_cast<size_t>(n));
+  std::vector<double> cost(static_cast<size_t>(n));
+  for (int i = 0; i < n; ++i) {
+    const int* cb = chi_b + size_t(i) * size_t(n_layers);
+    const int* ct = chi_t + size_t(i) * size_t(n_layers);
+    SweepLayout L;
+    const mera_status st = sweep_layout(n_layers, cb, ct, prec, &L);
+    if (st != MERA_OK) {
+      g_err = "MERA " + std::to_string(i) + ": " + g_err;
+      return st;
+    }
+    need[size_t(i)] = L.total;
+    cost[size_t(i)] = sweep_flops(n_layers, cb, ct, n_pow);
+  }
+  std::vector<int> order(static_cast<size_t>(n));
+  for (int i = 0; i < n; ++i) order[size_t(i)] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (need[size_t(a)] != need[size_t(b)]) return need[size_t(a)] > need[size_t(b)];
+    return cost[size_t(a)] > cost[size_t(b)];
+  });
+  std::vector<size_t> bytes;
+  std::vector<double> load;
+  size_t used = 0;
+  for (int i : order) {
+    const size_t b = need[size_t(i)];
+    if (int(bytes.size()) < max_lanes && b <= budget_bytes - used) {
+      lane[i] = int(bytes.size());
+      bytes.push_back(b);
+      load.push_back(cost[size_t(i)]);
+      used += b;
+      continue;
+    }
+    if (bytes.empty())
+      return fail(MERA_ENOMEM, "MERA %d needs %zu bytes of scratch; the budget is %zu", i, b, budget_bytes);
+    size_t best = 0;
+    for (size_t l = 1; l < load.size(); ++l)
+      if (load[l] < load[best]) best = l;
+    lane[i] = int(best);
+    load[best] += cost[size_t(i)];
+  }
+  *n_lanes = int(bytes.size());
+  for (size_t l = 0; l < bytes.size(); ++l) lane_bytes[l] = bytes[l];
+  return MERA_OK;
 }
 
 // Tile-width autotuner: every tensor-core GEMM step of the op's program that

@@ -361,3 +361,63 @@ def test_plans_carry_tile_widths():
                 assert st["bn"] == want
     plan = m.mera_plan_json(m.OP_ASCEND, 4, 4, m.PREC_F64)
     assert all(st["bn"] == 0 for dg in plan["diagrams"] for st in dg["steps"] if st["kind"] == "gemm")
+
+
+def _batch_dims(chis):
+    return [([b for b, _ in I.layer_dims(c)], [t for _, t in I.layer_dims(c)]) for c in chis]
+
+
+def _sweep_need(dims, prec):
+    return [m.mera_sweep_workspace_size(b, t, prec) for b, t in dims]
+
+
+def test_batch_lanes_one_per_mera_when_memory_allows():
+    dims = _batch_dims([8, 12, 16, 8])
+    need = _sweep_need(dims, m.PREC_BF16X3)
+    lanes, lane_bytes = m.mera_batch_lanes(dims, m.PREC_BF16X3, sum(need), max_lanes=32)
+    assert sorted(lanes) == [0, 1, 2, 3]
+    assert [lane_bytes[k] for k in lanes] == need
+
+
+def test_batch_lanes_single_lane_at_the_largest_scratch():
+    dims = _batch_dims([8, 16, 12, 16, 4])
+    need = _sweep_need(dims, m.PREC_BF16X3)
+    lanes, lane_bytes = m.mera_batch_lanes(dims, m.PREC_BF16X3, max(need), max_lanes=32)
+    assert lanes == [0] * 5 and lane_bytes == [max(need)]
+    with pytest.raises(m.MeraError, match="budget"):
+        m.mera_batch_lanes(dims, m.PREC_BF16X3, max(need) - 1)
+
+
+@pytest.mark.parametrize("budget_gb,max_lanes", [(40, 32), (120, 32), (200, 3), (200, 32), (1000, 8)])
+def test_batch_lanes_respect_budget_and_cover_every_member(budget_gb, max_lanes):
+    """32 MERAs with chi drawn from {8, 12, 16, 20, 24, 32}: lanes never exceed
+    the budget or the lane cap, and each lane's scratch holds every member."""
+    rng = np.random.default_rng(3)
+    chis = [int(rng.choice([8, 12, 16, 20, 24, 32])) for _ in range(32)]
+    dims = _batch_dims(chis)
+    need = _sweep_need(dims, m.PREC_BF16X3)
+    budget = budget_gb << 30
+    if max(need) > budget:
+        with pytest.raises(m.MeraError):
+            m.mera_batch_lanes(dims, m.PREC_BF16X3, budget, max_lanes)
+        return
+    lanes, lane_bytes = m.mera_batch_lanes(dims, m.PREC_BF16X3, budget, max_lanes)
+    assert 1 <= len(lane_bytes) <= max_lanes and sum(lane_bytes) <= budget
+    assert set(lanes) == set(range(len(lane_bytes)))
+    assert all(lane_bytes[k] >= n for k, n in zip(lanes, need))
+
+
+def test_batch_lanes_balance_equal_meras():
+    """Equal MERAs over k lanes: the list schedule deals them out evenly."""
+    dims = _batch_dims([12] * 11)
+    need = _sweep_need(dims, m.PREC_F64)[0]
+    lanes, lane_bytes = m.mera_batch_lanes(dims, m.PREC_F64, 100 * need, max_lanes=4)
+    counts = sorted(lanes.count(k) for k in range(len(lane_bytes)))
+    assert len(lane_bytes) == 4 and counts == [2, 3, 3, 3]
+
+
+def test_batch_lanes_reject_bad_dimensions():
+    dims = _batch_dims([8, 8])
+    dims[1] = ([4, 16, 8], [16, 9, 8])    # layers do not chain
+    with pytest.raises(m.MeraError, match="MERA 1"):
+        m.mera_batch_lanes(dims, m.PREC_F64, 1 << 40)

@@ -63,3 +63,89 @@ def test_operator_transpose():
     m.mera_op_transpose(_t(x).reshape(-1), d, out)
     want = np.transpose(x, (3, 4, 5, 0, 1, 2))
     assert np.array_equal(out.cpu().numpy().reshape(want.shape), want)
+
+
+# Map tolerances of the tensor-core modes (relative to the largest FP64 entry),
+# the same bounds the map parity tests derive from the operand and accumulator
+# precision of each mode.
+_MODE_TOL = {m.PREC_TF32: 5e-3, m.PREC_BF16X3: 5e-4}
+
+
+def _grads(h, rho, u, w, chi_b, chi_t, prec):
+    """Energy and its four gradients through MeraEnergy (forward + backward)."""
+    from paper_1906_12030_gb300.autograd import mera_energy
+
+    ts = [_t(x, True) for x in (h, rho, u, w)]
+    e = mera_energy(*ts, chi_b, chi_t, prec)
+    e.backward()
+    return e.item(), [t.grad.cpu().numpy() for t in ts]
+
+
+def test_adjoint_against_central_differences_chi12():
+    """FP64 adjoint at chi = 12 against central differences (step 1e-6) of the
+    oracle's energy, one random direction per input; general (non-symmetric)
+    h and rho so that the ket-side and bra-side holes both enter."""
+    chi = 12
+    rng = np.random.default_rng(80)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    h = I.random_operator(rng, chi, symmetric=False)
+    rho = I.random_operator(rng, chi, symmetric=False)
+    e, grads = _grads(h, rho, u, w, chi, chi, m.PREC_F64)
+    args = {"h": h, "rho": rho, "u": u, "w": w}
+    assert e == pytest.approx(O.energy(h, rho, u, w), rel=1e-10)
+    eps = 1e-6
+    for (name, x), g in zip(args.items(), grads):
+        d = rng.standard_normal(x.shape)
+        plus, minus = dict(args), dict(args)
+        plus[name], minus[name] = x + eps * d, x - eps * d
+        fd = (O.energy(**plus) - O.energy(**minus)) / (2 * eps)
+        assert float((g * d).sum()) == pytest.approx(fd, rel=1e-6), name
+
+
+@pytest.mark.parametrize("chi", [12, 16])
+def test_mixed_precision_adjoint_against_fp64(chi):
+    """The adjoint with TF32 and split-BF16 contractions (FP32 accumulation)
+    matches the FP64 adjoint entry by entry within each mode's map tolerance."""
+    rng = np.random.default_rng(81 + chi)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    h = I.random_operator(rng, chi, symmetric=False)
+    rho = I.random_operator(rng, chi, symmetric=False)
+    e64, g64 = _grads(h, rho, u, w, chi, chi, m.PREC_F64)
+    for prec, tol in _MODE_TOL.items():
+        e, gs = _grads(h, rho, u, w, chi, chi, prec)
+        for name, g, want in zip(("h", "rho", "u", "w"), gs, g64):
+            assert np.abs(g - want).max() <= tol * np.abs(want).max(), (prec, name)
+
+
+@pytest.mark.parametrize("prec", [m.PREC_TF32, m.PREC_BF16X3])
+def test_adjoint_at_chi24_recomputes_and_satisfies_euler_identities(prec):
+    """chi = 24, too large for an FP64 comparison: the forward keeps no
+    intermediate (only the inputs are saved; the backward recomputes every
+    rank-6 contraction), and the gradients obey Euler's identity for the
+    homogeneous polynomial E: degree 1 in h and rho, 4 in u (two ket- and two
+    bra-side disentanglers per diagram), 6 in w.  h is a rank-16 density and
+    rho a full-rank diagonal density: every final pairing (tr(A(h) rho) over
+    the positive diagonal, <D(rho), h> with D(rho) near the identity, and the
+    environments against u and w) is free of cancellation, so each identity
+    holds to the mode's relative map error."""
+    from paper_1906_12030_gb300.autograd import mera_energy
+
+    chi = 24
+    rng = np.random.default_rng(90)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    h = I.random_low_rank_density(rng, chi, 16)
+    rho = I.random_diagonal_density(rng, chi)
+    ts = [_t(x, True) for x in (h, rho, u, w)]
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    e = mera_energy(*ts, chi, chi, prec)
+    torch.cuda.synchronize()
+    kept = torch.cuda.memory_allocated() - before
+    assert kept < 1 << 20, kept          # a chi^6 intermediate would be 1.5 GB
+    e.backward()
+    ev = e.item()
+    assert ev > 0
+    degree = {"h": 1, "rho": 1, "u": 4, "w": 6}
+    for (name, k), x, t in zip(degree.items(), (h, rho, u, w), ts):
+        lhs = float(torch.sum(t.grad * t.detach()))
+        assert lhs == pytest.approx(k * ev, rel=_MODE_TOL[prec]), (name, lhs, k * ev)

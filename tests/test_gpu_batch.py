@@ -80,3 +80,47 @@ def test_batched_energies_respect_exact_bound():
         e0 = O.exact_energy_per_spin(hz)
         assert e_site >= e0 - 1e-12
         assert e_site < 0.6 * e0  # well down from the random start (about 0.05 e0)
+
+
+def test_lanes_share_scratch_and_match_lone_sweeps():
+    """A budget of twice the largest scratch forces lanes: MERAs of one lane
+    share a buffer and a stream, and every result is still exactly the lone
+    sweep's."""
+    prec = m.PREC_BF16X3
+    rng = np.random.default_rng(82)
+    specs = [(20 + s, int(rng.choice([4, 6, 8])), float(rng.uniform(0.9, 1.1))) for s in range(6)]
+    batch = [_mera(*sp) for sp in specs]
+    alone = [_mera(*sp) for sp in specs]
+    states = [b[0] for b in batch]
+    need = [m.mera_sweep_workspace_size(st.chi_b, st.chi_t, prec) for st in states]
+    wss, streams = m.batch_resources(states, prec, budget_bytes=2 * max(need))
+    assert 1 < len({id(s) for s in streams}) < len(states)
+    eb = torch.empty(len(specs), dtype=torch.float64, device="cuda")
+    ea = torch.empty(1, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        try:
+            m.mera_sweep_batch(states, [b[1] for b in batch], [b[2] for b in batch], 20, eb, prec=prec, wss=wss,
+                               streams=streams, n_threads=4)
+        except m.MeraNotConverged:
+            pass
+        energies = []
+        for st, h1, shift in alone:
+            _sweep(st, h1, shift, ea, prec)
+            energies.append(ea.item())
+        torch.cuda.synchronize()
+        assert eb.cpu().tolist() == energies
+    for sb, (sa, _, _) in zip(states, alone):
+        for x, y in zip(sb.us + sb.ws + [sb.rho_star], sa.us + sa.ws + [sa.rho_star]):
+            assert torch.equal(x, y)
+
+
+def test_scratch_shared_across_streams_is_rejected():
+    batch = [_mera(30 + s, 4, 1.0) for s in range(2)]
+    st0 = batch[0][0]
+    ws = m.workspace(m.mera_sweep_workspace_size(st0.chi_b, st0.chi_t, m.PREC_F64))
+    e = torch.zeros(2, dtype=torch.float64, device="cuda")
+    n0 = m.mera_launch_count()
+    with pytest.raises(m.MeraError, match="another stream"):
+        m.mera_sweep_batch([b[0] for b in batch], [b[1] for b in batch], [b[2] for b in batch], 20, e,
+                           wss=[ws, ws], streams=[torch.cuda.Stream(), torch.cuda.Stream()])
+    assert m.mera_launch_count() == n0

@@ -56,6 +56,9 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip the replayed-graph timing of the sweep")
     ap.add_argument("--tune", action="store_true", help="--case ascend|descend|env_u|env_w: autotune the map first")
+    ap.add_argument("--widths", default=None,
+                    help="JSON file of tile widths (from --save-widths) to record instead of autotuning")
+    ap.add_argument("--save-widths", default=None, help="write the autotuned tile widths to this JSON file")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the library's tile-width autotuner (run on the sweep's maps before timing)")
     ap.add_argument("--sweeps", type=int, default=300, help="--case precision: optimisation sweeps per run")
@@ -319,16 +322,25 @@ def run_native(args):
         # the library's tile-width autotuner, once, on every map of the sweep;
         # record which chi^9-class steps it moved off the planner's width
         n_shapes, moved = 0, set()
-        for cb, ct in I.layer_dims(chi):
-            for op in (m.OP_ASCEND, m.OP_DESCEND, m.OP_ENV_U, m.OP_ENV_W):
-                n_shapes += m.mera_autotune(op, cb, ct, prec, device=dev)
+        if args.widths:  # recorded widths of an earlier run, set without timing
+            with open(args.widths) as f:
+                for pr, M, N, K, cf, bn in json.load(f):
+                    m.mera_set_tile_width(pr, M, N, K, cf, bn)
+                    n_shapes += 1
+        else:
+            for cb, ct in I.layer_dims(chi):
+                for op in (m.OP_ASCEND, m.OP_DESCEND, m.OP_ENV_U, m.OP_ENV_W):
+                    n_shapes += m.mera_autotune(op, cb, ct, prec, device=dev)
+        if args.save_widths and local == 0:
+            with open(args.save_widths, "w") as f:
+                json.dump([list(x) for x in m.mera_tile_widths()], f)
         for cb, ct in I.layer_dims(chi):
             for op in (m.OP_ASCEND, m.OP_DESCEND, m.OP_ENV_U, m.OP_ENV_W):
                 for dg in m.mera_plan_json(op, cb, ct, prec)["diagrams"]:
                     for st in dg["steps"]:
                         if st["kind"] == "gemm" and st["bn"] != _heuristic_bn(args.prec, st["N"]):
                             moved.add((st["M"], st["N"], st["K"], st["bn"], bool(st["dominant"])))
-        tuned = {"shapes_timed": n_shapes, "moved": sorted(moved)}
+        tuned = {"shapes_timed" if not args.widths else "shapes_loaded": n_shapes, "moved": sorted(moved)}
     us, ws_, rho, e, sweep = make_state(prec)
     energies = []
     for _ in range(args.warmup):

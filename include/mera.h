@@ -416,6 +416,23 @@ mera_status mera_autotune(int op, int chi_b, int chi_t, int prec, double* out_sc
 mera_status mera_autotune_reset(void);
 
 /*
+ * Recorded tile widths, set and read without timing (host only): to carry
+ * the autotuner's results from one process to another, or to reproduce them
+ * where timings would be distorted (under a profiler).
+ * mera_set_tile_width records width bn for the GEMM shape (prec, M, N, K,
+ * c_final: 1 when the step writes the caller's binary64 output); bn = 0
+ * forgets it.  Accepted widths are the autotuner's candidates: 256 (not
+ * MERA_PREC_BF16X6), 128 or 64 for N > 128; 128 or 64 for 64 < N <= 128;
+ * none for N <= 64.  MERA_EINVAL otherwise, and for MERA_PREC_F64.
+ * mera_tile_widths writes *n, the number of recorded shapes, and the first
+ * min(*n, cap) of them to out as six values each: prec, M, N, K, c_final,
+ * width.  mera_set_tile_width discards cached programs like mera_autotune;
+ * call it when no call of this library is in flight.
+ */
+mera_status mera_set_tile_width(int prec, long long M, long long N, long long K, int c_final, int bn);
+mera_status mera_tile_widths(long long* out, int cap, int* n);
+
+/*
  * Memory knob (no counterpart in the paper): a rank-7 intermediate of the
  * chi^9 contraction pairs larger than `bytes` (default 16 GiB) is computed
  * one slice at a time -- the pair runs once per value of one of its free

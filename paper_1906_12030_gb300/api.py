@@ -22,7 +22,7 @@ __all__ = [
     "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE", "mera_device_status", "mera_gemm_test",
     "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_sweep_batch", "mera_set_slice_bytes", "MeraGraph", "mera_sweep_graph", "mera_stiefel_step",
     "mera_stiefel_workspace_size", "mera_sweep_riemannian", "mera_autotune", "mera_autotune_reset",
-    "mera_batch_lanes", "batch_resources",
+    "mera_batch_lanes", "batch_resources", "mera_set_tile_width", "mera_tile_widths",
 ]
 
 PREC_F64, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3, 4
@@ -109,6 +109,8 @@ def library():
             "mera_sweep_riemannian": ([ctypes.POINTER(_State), vp, d, i, i, d, vp, sz, vp, vp], i),
             "mera_autotune": ([i, i, i, i, vp, sz, vp, sz, vp, ctypes.POINTER(i)], i),
             "mera_autotune_reset": ([], i),
+            "mera_set_tile_width": ([i, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, i, i], i),
+            "mera_tile_widths": ([ctypes.POINTER(ctypes.c_longlong), i, ctypes.POINTER(i)], i),
             "mera_sweep_batch": ([ctypes.POINTER(_State), i, ctypes.POINTER(vp), ctypes.POINTER(d), i, i,
                                   ctypes.POINTER(vp), ctypes.POINTER(sz), vp, ctypes.POINTER(vp), i], i),
             "mera_batch_lanes": ([i, i, ctypes.POINTER(i), ctypes.POINTER(i), i, i, sz, i, ctypes.POINTER(i),
@@ -410,6 +412,20 @@ def mera_autotune(op: int, chi_b: int, chi_t: int, prec: int, device=None, strea
 
 def mera_autotune_reset() -> None:
     _check(library().mera_autotune_reset())
+
+
+def mera_set_tile_width(prec: int, M: int, N: int, K: int, c_final: bool, bn: int) -> None:
+    """Record tile width bn for a GEMM shape without timing (0 forgets it)."""
+    _check(library().mera_set_tile_width(prec, M, N, K, int(bool(c_final)), bn))
+
+
+def mera_tile_widths() -> list:
+    """Every recorded width as (prec, M, N, K, c_final, width)."""
+    n = ctypes.c_int(0)
+    _check(library().mera_tile_widths(None, 0, ctypes.byref(n)))
+    buf = (ctypes.c_longlong * (6 * max(n.value, 1)))()
+    _check(library().mera_tile_widths(buf, n.value, ctypes.byref(n)))
+    return [tuple(int(x) for x in buf[6 * k:6 * k + 6]) for k in range(n.value)]
 
 
 def mera_launch_count() -> int:

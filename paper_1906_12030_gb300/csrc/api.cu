@@ -1098,6 +1098,29 @@ extern "C" mera_status mera_autotune_reset(void) {
   return MERA_OK;
 }
 
+// Recorded widths set or read directly: the autotuner's candidates only.
+extern "C" mera_status mera_set_tile_width(int prec, long long M, long long N, long long K, int c_final, int bn) {
+  if (!prec_ok(prec) || prec == PREC_F64) return fail(MERA_EINVAL, "tile widths apply to the tensor-core modes");
+  if (M < 1 || N < 1 || K < 1 || (c_final != 0 && c_final != 1)) return fail(MERA_EINVAL, "bad GEMM shape");
+  if (bn != 0) {
+    const bool ok = N > 128  ? (bn == 128 || bn == 64 || (bn == 256 && prec != PREC_BF16X6))
+                    : N > 64 ? (bn == 128 || bn == 64)
+                             : false;
+    if (!ok) return fail(MERA_EINVAL, "width %d is not an autotuner candidate for N = %lld", bn, N);
+  }
+  set_tuned_tile(prec, M, N, K, c_final, bn);
+  return MERA_OK;
+}
+
+extern "C" mera_status mera_tile_widths(long long* out, int cap, int* n) {
+  if (!n || cap < 0 || (cap > 0 && !out)) return fail(MERA_EINVAL, "bad arguments");
+  const std::vector<std::vector<int64_t>> v = tuned_tiles();
+  *n = int(v.size());
+  for (size_t i = 0; i < v.size() && int(i) < cap; ++i)
+    for (size_t j = 0; j < 6; ++j) out[6 * i + j] = static_cast<long long>(v[i][j]);
+  return MERA_OK;
+}
+
 extern "C" mera_status mera_set_slice_bytes(size_t bytes) {
   set_slice_bytes(bytes);
   return MERA_OK;

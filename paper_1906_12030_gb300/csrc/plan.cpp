@@ -807,6 +807,15 @@ int tuned_tile_count() {
   return int(g_tuned.size());
 }
 
+std::vector<std::vector<int64_t>> tuned_tiles() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::vector<std::vector<int64_t>> out;
+  for (const auto& kv : g_tuned)
+    out.push_back({std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), std::get<3>(kv.first),
+                   std::get<4>(kv.first), kv.second});
+  return out;
+}
+
 void set_slice_bytes(size_t bytes) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_slice_bytes = bytes;

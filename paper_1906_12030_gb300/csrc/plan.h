@@ -112,6 +112,8 @@ int tc_tile_n(int prec, int64_t M, int64_t N, int64_t K, int c_final);
 void set_tuned_tile(int prec, int64_t M, int64_t N, int64_t K, int c_final, int bn);
 void clear_tuned_tiles();
 int tuned_tile_count();
+// Every recorded width as (prec, M, N, K, c_final, width), in key order.
+std::vector<std::vector<int64_t>> tuned_tiles();
 int planes(int prec);       // 2 for BF16X3 (hi, lo), 3 for BF16X6 (hi, mid, lo), else 1
 
 // Builds (and caches) the program; thread safe.  Returns nullptr on bad input.

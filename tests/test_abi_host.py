@@ -421,3 +421,35 @@ def test_batch_lanes_reject_bad_dimensions():
     dims[1] = ([4, 16, 8], [16, 9, 8])    # layers do not chain
     with pytest.raises(m.MeraError, match="MERA 1"):
         m.mera_batch_lanes(dims, m.PREC_F64, 1 << 40)
+
+
+def _gemm_steps(op, chi, prec):
+    return [st for dg in m.mera_plan_json(op, chi, chi, prec)["diagrams"] for st in dg["steps"] if st["kind"] == "gemm"]
+
+
+def test_recorded_tile_widths_set_read_and_reach_the_plan():
+    prec = m.PREC_BF16X3
+    m.mera_autotune_reset()
+    try:
+        st = next(s for s in _gemm_steps(m.OP_ASCEND, 16, prec) if s["N"] > 128 and s["split"] == 1)
+        cf = int(st["c_buf"] < 0)
+        new = 128 if st["bn"] != 128 else 64
+        m.mera_set_tile_width(prec, st["M"], st["N"], st["K"], cf, new)
+        assert m.mera_tile_widths() == [(prec, st["M"], st["N"], st["K"], cf, new)]
+        same = [s for s in _gemm_steps(m.OP_ASCEND, 16, prec)
+                if (s["M"], s["N"], s["K"], int(s["c_buf"] < 0)) == (st["M"], st["N"], st["K"], cf)]
+        assert same and all(s["bn"] == new for s in same)
+        m.mera_set_tile_width(prec, st["M"], st["N"], st["K"], cf, 0)      # forget
+        assert m.mera_tile_widths() == []
+        assert all(s["bn"] == st["bn"] for s in _gemm_steps(m.OP_ASCEND, 16, prec)
+                   if (s["M"], s["N"], s["K"], int(s["c_buf"] < 0)) == (st["M"], st["N"], st["K"], cf))
+    finally:
+        m.mera_autotune_reset()
+
+
+@pytest.mark.parametrize("prec,N,bn", [(m.PREC_F64, 256, 128), (m.PREC_BF16X3, 64, 64), (m.PREC_BF16X3, 100, 256),
+                                       (m.PREC_BF16X6, 512, 256), (m.PREC_TF32, 512, 96)])
+def test_tile_widths_outside_the_candidates_are_rejected(prec, N, bn):
+    with pytest.raises(m.MeraError):
+        m.mera_set_tile_width(prec, 4096, N, 256, 0, bn)
+    assert m.mera_tile_widths() == []

@@ -31,9 +31,13 @@ reading fixed from its text, equations and contribution counts:
   manifold, an alternative update (not the paper's), pinned by tangency, the
   retraction and its first-order decrease of the energy.
 
-Parity unpinned: the Ising-CFT scaling dimensions (1/8, 1, 9/8) are not
-reached by optimisations the oracle can run, so they pin nothing here (the
-dimensions of the identity, 0, and of exactly solvable cases are pinned).
+Pinned against the physics: a chi = 4 MERA that the oracle optimises from a
+parity-symmetric start (tests/golden/make_chi4_z2_mera.py) lies within 1e-4
+of the exact energy density -4/pi, and the scale-invariant ascending map of
+its top layer gives the Ising-CFT scaling dimensions 1/8, 1 and the pair near
+9/8 within 1-3 %.  Higher accuracy would need larger chi and longer runs than
+the oracle can afford, so the paper's own figures (5e-10 at chi = 16) pin
+nothing here.
 """
 from __future__ import annotations
 

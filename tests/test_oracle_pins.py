@@ -408,3 +408,42 @@ def test_z2_symmetric_start_is_kept_by_the_sweep():
         assert np.abs(W[pair[:, None] != pt[None, :]]).max() < 1e-12
         assert np.abs(U[pair[:, None] != pair[None, :]]).max() < 1e-12
         pb = pt
+
+
+# --------------------------------------------------------------------------
+# Physics near convergence: a chi = 4 MERA optimised by the oracle alone
+# (tests/golden/make_chi4_z2_mera.py: parity-symmetric start, 2900 sweeps)
+# reproduces the Ising CFT read off the scale-invariant ascending map
+# (Sec. II B: Delta_sigma = 1/8, Delta_eps = 1, the sigma descendants at
+# 9/8) and the exact energy density -4/pi (Sec. III A).  The stored state
+# only saves the CPU time of the first sweeps; the test sweeps on from it.
+# --------------------------------------------------------------------------
+CHI4 = os.path.join(os.path.dirname(__file__), "golden", "mera_chi4_z2.json")
+
+
+def test_converged_chi4_mera_reproduces_the_ising_cft():
+    gold = json.load(open(GOLDEN))
+    doc = json.load(open(CHI4))
+    layers = [(np.array(x["u"]).reshape((x["chi_b"],) * 4), np.array(x["w"]).reshape(x["chi_b"], x["chi_b"], x["chi_t"]))
+              for x in doc["layers"]]
+    rho = np.array(doc["rho_star"]).reshape((doc["chi"],) * 6)
+    h1, shift = O.ising_h1(1.0)
+    exact = gold["e_exact_per_spin"]["value"]
+    e_start = O.energy_per_spin(layers, h1, shift, rho, 100)
+    assert e_start == pytest.approx(doc["energy_per_spin"], abs=1e-12)
+    for _ in range(100):
+        layers, rho, _ = O.sweep(layers, h1, shift, rho, 20)
+    e = O.energy_per_spin(layers, h1, shift, rho, 100)
+    # 100 more sweeps keep lowering the energy, which stays above -4/pi
+    assert exact < e < e_start
+    assert (e - exact) / abs(exact) < 1.2e-4
+    for u, w in layers:
+        um, wm = u.reshape(u.shape[0] ** 2, -1), w.reshape(w.shape[0] ** 2, -1)
+        assert np.abs(um.T @ um - np.eye(um.shape[1])).max() < 1e-12
+        assert np.abs(wm.T @ wm - np.eye(wm.shape[1])).max() < 1e-12
+    dims = O.scaling_dimensions(*layers[-1], 6)
+    d_id, d_sigma, d_eps = gold["ising_cft_scaling_dims"]["value"]
+    assert dims[0] == pytest.approx(d_id, abs=1e-9)
+    assert abs(dims[1] - d_sigma) < 0.01
+    assert abs(dims[2] - d_eps) < 0.02
+    assert np.all(np.abs(dims[3:5] - gold["sigma_descendant"]["value"]) < 0.04)

@@ -576,8 +576,9 @@ def run_case(args):
     dom, allg, perm = (m.mera_profile_read(k) for k in (m.PROF_GEMM_DOMINANT, m.PROF_GEMM, m.PROF_PERMUTE))
     m.mera_profile_enable(False)
     fl = m.mera_flops(op, chi, chi)
+    dom_tf = dom[2] / dom[1] / 1e9 if dom[1] else None
     print(json.dumps({"case": args.case, "chi": chi, "prec": args.prec, "ms": ms, "tflops": fl / ms / 1e9,
-                      "dominant": {"launches": dom[0], "ms": dom[1], "tflops": dom[2] / dom[1] / 1e9 if dom[1] else None},
+                      "dominant": {"launches": dom[0], "ms": dom[1], "tflops": dom_tf},
                       "gemm_ms": allg[1], "permute_ms": perm[1], "device_status": m.mera_device_status()}), flush=True)
 
 

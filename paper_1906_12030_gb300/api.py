@@ -20,7 +20,8 @@ __all__ = [
     "mera_energy", "mera_ising_h1", "mera_sweep", "mera_sweep_workspace_size", "mera_plan_json", "mera_flops",
     "workspace", "MeraState", "mera_launch_count", "mera_profile_enable", "mera_profile_read",
     "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE", "mera_device_status", "mera_gemm_test",
-    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_sweep_batch", "mera_set_slice_bytes", "MeraGraph", "mera_sweep_graph", "mera_stiefel_step",
+    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_sweep_batch", "mera_set_slice_bytes",
+    "MeraGraph", "mera_sweep_graph", "mera_stiefel_step",
     "mera_stiefel_workspace_size", "mera_sweep_riemannian", "mera_autotune", "mera_autotune_reset",
     "mera_batch_lanes", "batch_resources", "mera_set_tile_width", "mera_tile_widths",
 ]

@@ -424,8 +424,8 @@ CHI4 = os.path.join(os.path.dirname(__file__), "golden", "mera_chi4_z2.json")
 def test_converged_chi4_mera_reproduces_the_ising_cft():
     gold = json.load(open(GOLDEN))
     doc = json.load(open(CHI4))
-    layers = [(np.array(x["u"]).reshape((x["chi_b"],) * 4), np.array(x["w"]).reshape(x["chi_b"], x["chi_b"], x["chi_t"]))
-              for x in doc["layers"]]
+    layers = [(np.array(x["u"]).reshape((x["chi_b"],) * 4),
+               np.array(x["w"]).reshape(x["chi_b"], x["chi_b"], x["chi_t"])) for x in doc["layers"]]
     rho = np.array(doc["rho_star"]).reshape((doc["chi"],) * 6)
     h1, shift = O.ising_h1(1.0)
     exact = gold["e_exact_per_spin"]["value"]

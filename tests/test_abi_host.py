@@ -453,3 +453,32 @@ def test_tile_widths_outside_the_candidates_are_rejected(prec, N, bn):
     with pytest.raises(m.MeraError):
         m.mera_set_tile_width(prec, 4096, N, 256, 0, bn)
     assert m.mera_tile_widths() == []
+
+
+def _imports(path):
+    import ast
+
+    tree = ast.parse(open(path).read())
+    out = set()
+    for node in ast.walk(tree):
+        if isinstance(node, ast.Import):
+            out |= {a.name.split(".")[0] for a in node.names}
+        elif isinstance(node, ast.ImportFrom) and node.module and node.level == 0:
+            out.add(node.module.split(".")[0])
+    return out
+
+
+def test_product_and_oracle_share_no_code():
+    """The package never imports the oracle, the oracle never imports the
+    package, and the native sources never name the oracle."""
+    pkg = os.path.join(ROOT, "paper_1906_12030_gb300")
+    for name in os.listdir(pkg):
+        if name.endswith(".py"):
+            assert "oracle" not in _imports(os.path.join(pkg, name)), name
+    for name in os.listdir(os.path.join(ROOT, "oracle")):
+        if name.endswith(".py"):
+            assert "paper_1906_12030_gb300" not in _imports(os.path.join(ROOT, "oracle", name)), name
+    csrc = os.path.join(pkg, "csrc")
+    for name in os.listdir(csrc):
+        assert "oracle" not in open(os.path.join(csrc, name), errors="replace").read().lower(), name
+    assert _imports(os.path.join(ROOT, "mera_inputs.py")) <= {"__future__", "numpy"}

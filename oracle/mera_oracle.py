@@ -32,10 +32,10 @@ reading fixed from its text, equations and contribution counts:
   retraction and its first-order decrease of the energy.
 
 Pinned against the physics: a chi = 4 MERA that the oracle optimises from a
-parity-symmetric start (tests/golden/make_chi4_z2_mera.py) lies within 1e-4
+parity-symmetric start (tests/golden/make_chi4_z2_mera.py) lies within 6e-6
 of the exact energy density -4/pi, and the scale-invariant ascending map of
-its top layer gives the Ising-CFT scaling dimensions 1/8, 1 and the pair near
-9/8 within 1-3 %.  Higher accuracy would need larger chi and longer runs than
+its top layer gives the Ising-CFT scaling dimensions 1/8, 1 and the pair at
+9/8 within 1 %.  Higher accuracy would need larger chi and longer runs than
 the oracle can afford, so the paper's own figures (5e-10 at chi = 16) pin
 nothing here.
 """

@@ -7,7 +7,7 @@ steps of rho* each).  The file holds every layer's u and w, rho*, and the
 oracle's energy per spin of the final state.  Only oracle/ and the seeded
 input generators are called.
 
-    python tests/golden/make_chi4_z2_mera.py      # about 3 minutes on 8 cores
+    python tests/golden/make_chi4_z2_mera.py      # about 10 minutes on 8 cores
 """
 import json
 import os
@@ -19,7 +19,7 @@ sys.path.insert(0, ROOT)
 import mera_inputs as I  # noqa: E402
 from oracle import mera_oracle as O  # noqa: E402
 
-SEED, CHI, SWEEPS, N_POW = 0, 4, 2900, 20
+SEED, CHI, SWEEPS, N_POW = 0, 4, 8900, 20
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "mera_chi4_z2.json")
 
 

@@ -27,3 +27,22 @@ def test_reference_arm_prints_the_contract_line():
     assert line["e2e"] == {"value": line["value"], "unit": "sweep/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert "chi=6" in line["config"]["workload"]
+
+
+def test_reported_planner_widths_match_the_planner():
+    """bench.py reports which GEMM shapes the autotuner moved by comparing
+    each planned width with its copy of the planner's rule; the copy must
+    agree with every untuned plan."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import paper_1906_12030_gb300 as m
+
+    m.mera_autotune_reset()
+    for name in ("tf32", "bf16", "bf16x3", "bf16x6"):
+        prec = m.PRECS[name]
+        for chi_b, chi_t in ((4, 16), (16, 16), (8, 8), (3, 5)):
+            for op in (m.OP_ASCEND, m.OP_DESCEND, m.OP_ENV_U, m.OP_ENV_W):
+                for dg in m.mera_plan_json(op, chi_b, chi_t, prec)["diagrams"]:
+                    for st in dg["steps"]:
+                        if st["kind"] == "gemm":
+                            assert st["bn"] == bench._heuristic_bn(name, st["N"]), (name, op, st["N"])

@@ -93,6 +93,29 @@ def test_exact_energy_off_critical_against_exact_diagonalisation():
     assert O.exact_energy_per_spin(hz) == pytest.approx(e0, abs=3e-7)
 
 
+@pytest.mark.parametrize("theta,hz", [(0.0, 1.0), (np.pi / 4, 1.0), (0.3, 0.5), (1.1, 2.0)])
+def test_product_state_mera_energy_closed_form(theta, hz):
+    """A bond-dimension-1 MERA is a product state: w of the bottom layer maps
+    the coarse site to phi (x) phi with phi = (cos t, sin t) per spin, every
+    other tensor is 1 (or the identity disentangler).  For such a state
+    <Z> = cos 2t and <X> = sin 2t on every spin, so the energy per spin of
+    H = -sum X X - h sum Z is -sin^2(2t) - h cos(2t).  This runs the whole
+    oracle pipeline -- rho* of the SI layer, descent through chi_t = 1, the
+    blocked 3-site density, the shift and the per-spin factor -- against a
+    closed form."""
+    phi2 = np.array([np.cos(theta), np.sin(theta)])
+    phi = np.kron(phi2, phi2)                               # blocked site: two spins
+    w1 = np.einsum("a,b->ab", phi, phi).reshape(4, 4, 1)
+    u1 = np.eye(16).reshape(4, 4, 4, 4)
+    one_u, one_w = np.ones((1, 1, 1, 1)), np.ones((1, 1, 1))
+    layers = [(u1, w1), (one_u, one_w), (one_u, one_w)]
+    h1, shift = O.ising_h1(hz)
+    e = O.energy_per_spin(layers, h1, shift, O.identity_density(1), n_pow=3)
+    want = -np.sin(2 * theta) ** 2 - hz * np.cos(2 * theta)
+    assert e == pytest.approx(want, abs=1e-13)
+    assert e >= O.exact_energy_per_spin(hz) - 1e-13      # variational
+
+
 # --------------------------------------------------------------------------
 # Superoperators: invariants.
 # --------------------------------------------------------------------------

@@ -482,3 +482,22 @@ def test_product_and_oracle_share_no_code():
     for name in os.listdir(csrc):
         assert "oracle" not in open(os.path.join(csrc, name), errors="replace").read().lower(), name
     assert _imports(os.path.join(ROOT, "mera_inputs.py")) <= {"__future__", "numpy"}
+
+
+def test_plain_c_consumer_builds_and_runs(tmp_path):
+    """tests/c/abi_consumer.c: the header compiles as strict C11, the library
+    links from C, and the host-only entry points answer as documented."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lib_dir = os.path.dirname(m.library_path())
+    exe = str(tmp_path / "abi_consumer")
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c", "abi_consumer.c"), "-L", lib_dir, "-lmera", "-lm",
+                    f"-Wl,-rpath,{lib_dir}", "-o", exe], check=True, capture_output=True, text=True)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "abi consumer ok"

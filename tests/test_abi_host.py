@@ -501,3 +501,18 @@ def test_plain_c_consumer_builds_and_runs(tmp_path):
     out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0, out.stderr
     assert out.stdout.strip() == "abi consumer ok"
+
+
+def test_library_exports_nothing_undeclared():
+    """Every exported mera_* symbol of the shared library is declared (and so
+    documented) in include/mera.h."""
+    import shutil
+    import subprocess
+
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("no nm")
+    out = subprocess.run([nm, "-D", "--defined-only", m.library_path()], check=True, capture_output=True,
+                         text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.split() and ln.split()[-1].startswith("mera_")}
+    assert exported == set(_declared_symbols())

@@ -217,6 +217,58 @@ def env_u(h, rho, u, w):
     return 0.5 * g
 
 
+def _fixed(specs, ops, out, fixed):
+    """The network with the legs in `fixed` (letter -> index) held at one
+    value: every operand carrying such a leg is sliced there, and the leg
+    leaves the output.  Costs the whole network divided by the fixed legs'
+    dimensions."""
+    specs2, ops2 = [], []
+    for sp, op in zip(specs, ops):
+        for letter, idx in fixed.items():
+            if letter in sp:
+                op = np.take(op, idx, axis=sp.index(letter))
+                sp = sp.replace(letter, "")
+        specs2.append(sp)
+        ops2.append(op)
+    out2 = "".join(c for c in out if c not in fixed)
+    return _ein(",".join(specs2) + "->" + out2, *ops2)
+
+
+def env_w_cols(h, rho, u, w, cols):
+    """Gamma_w[:, :, c] for each c in `cols`: env_w's six networks with the
+    removed isometry's upper leg fixed (used to check full-size results entry
+    by entry)."""
+    out = []
+    for c in cols:
+        g = 0.0
+        for case in ("even", "odd"):
+            for k in range(3):
+                bw = list(_BRA_W)
+                hole = bw.pop(k)
+                specs = _KET_W + _KET_U[case] + [_OP] + list(_BRA_U[case]) + bw + ["stvpqr"]
+                ops = [w, w, w, u, u, h, u, u, w, w, rho]
+                g = g + _fixed(specs, ops, hole, {hole[2]: c})
+        out.append(0.5 * g)
+    return np.stack(out)
+
+
+def env_u_rows(h, rho, u, w, rows):
+    """Gamma_u[a, b, :, :] for each (a, b) in `rows`: env_u's four networks
+    with the removed disentangler's lower legs fixed."""
+    out = []
+    for a, b in rows:
+        g = 0.0
+        for case in ("even", "odd"):
+            for k in range(2):
+                bu = list(_BRA_U[case])
+                hole = bu.pop(k)
+                specs = _KET_W + _KET_U[case] + [_OP] + bu + list(_BRA_W) + ["stvpqr"]
+                ops = [w, w, w, u, u, h, u, w, w, w, rho]
+                g = g + _fixed(specs, ops, hole, {hole[0]: a, hole[1]: b})
+        out.append(0.5 * g)
+    return np.stack(out)
+
+
 # ---------------------------------------------------------------------------
 # Update (Fig. 5): SVD of the environment, new tensor from U and V.
 # ---------------------------------------------------------------------------

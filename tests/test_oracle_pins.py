@@ -471,3 +471,26 @@ def test_converged_chi4_mera_reproduces_the_ising_cft():
     assert abs(dims[2] - d_eps) < 0.002
     assert np.all(np.abs(dims[3:5] - gold["sigma_descendant"]["value"]) < 0.005)
     assert dims[5] > 1.5      # then a gap: no other primary or descendant below 3/2
+
+
+# --------------------------------------------------------------------------
+# Entry-wise helpers for full-size checks: ascend_rows, env_w_cols and
+# env_u_rows compute parts of the (pinned) maps with some legs held fixed.
+# They must equal the corresponding parts of the whole maps.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("chi_b,chi_t", [(3, 3), (2, 3), (4, 5), (3, 2)])
+def test_row_and_column_helpers_equal_the_whole_maps(chi_b, chi_t):
+    rng = _rng(100 + 10 * chi_b + chi_t)
+    u, w = I.random_u(rng, chi_b), I.random_w(rng, chi_b, chi_t)
+    h = I.random_operator(rng, chi_b, symmetric=False)
+    rho = I.random_operator(rng, chi_t, symmetric=False)
+    a, gw, gu = O.ascend(h, u, w), O.env_w(h, rho, u, w), O.env_u(h, rho, u, w)
+    rows3 = [(0, 0, 0), (chi_t - 1, 0, chi_t - 1)]
+    for k, (p, q, r) in enumerate(rows3):
+        assert np.abs(O.ascend_rows(h, u, w, rows3)[k] - a[p, q, r]).max() < 1e-12
+    cols = [0, chi_t - 1]
+    for k, c in enumerate(O.env_w_cols(h, rho, u, w, cols)):
+        assert np.abs(c - gw[:, :, cols[k]]).max() < 1e-12
+    rows2 = [(0, 0), (chi_b - 1, 0), (1, chi_b - 1)]
+    for k, r in enumerate(O.env_u_rows(h, rho, u, w, rows2)):
+        assert np.abs(r - gu[rows2[k]]).max() < 1e-12

@@ -297,3 +297,31 @@ def test_autotuned_widths_are_bit_identical_at_full_size():
             assert float((a0 - a1).abs().max()) <= MAP_TOL[prec] * float(a0.abs().max())
     finally:
         m.mera_autotune_reset()
+
+
+def test_chi16_sampled_environments():
+    """chi = 16, the benchmarked size: rows of Gamma_u and a column of Gamma_w
+    from the library (FP64 and BF16X3, the environments of every sweep) against
+    the oracle's entry-wise helpers (the whole maps cost minutes on the CPU).
+    Tolerances are relative to the largest sampled oracle entry."""
+    chi = 16
+    rng = np.random.default_rng(91)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    h, rho = I.random_operator(rng, chi), I.random_density(rng, chi)
+    rows, cols = [(0, 0), (7, 12)], [5]
+    want_u = O.env_u_rows(h, rho, u, w, rows)
+    want_w = O.env_w_cols(h, rho, u, w, cols)
+    su, sw = np.abs(want_u).max(), np.abs(want_w).max()
+    d = lambda x: _cuda(x).reshape(-1)  # noqa: E731
+    ud, wd, hd, rd = d(u), d(w), d(h), d(rho)
+    for prec, tol in ((m.PREC_F64, 1e-10), (m.PREC_BF16X3, MAP_TOL[m.PREC_BF16X3])):
+        gu = torch.empty(chi ** 4, dtype=torch.float64, device="cuda")
+        gw = torch.empty(chi ** 3, dtype=torch.float64, device="cuda")
+        m.mera_env_u(hd, rd, ud, wd, chi, chi, gu, prec=prec)
+        m.mera_env_w(hd, rd, ud, wd, chi, chi, gw, prec=prec)
+        gu = gu.cpu().numpy().reshape((chi,) * 4)
+        gw = gw.cpu().numpy().reshape(chi, chi, chi)
+        for k, (a, b) in enumerate(rows):
+            assert np.abs(gu[a, b] - want_u[k]).max() <= tol * su, (prec, a, b)
+        for k, c in enumerate(cols):
+            assert np.abs(gw[:, :, c] - want_w[k]).max() <= tol * sw, (prec, c)

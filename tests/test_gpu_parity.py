@@ -231,3 +231,29 @@ def test_scaling_dimensions_match_oracle(chi):
     want = O.scaling_dimensions(u, w, 10)[:4]
     assert got[0] == pytest.approx(0.0, abs=1e-9)  # A(1) = 1
     np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-8)
+
+
+def test_scaling_dimensions_of_the_optimised_chi4_mera():
+    """The stored chi = 4 MERA that the oracle optimised (tests/golden): the
+    GPU Arnoldi gives the oracle's leading dimensions of its scale-invariant
+    layer and, with them, the Ising CFT values (Sec. II B): 0, 1/8, 1 and the
+    two sigma descendants at 9/8, before a gap."""
+    import json
+    import os
+
+    from paper_1906_12030_gb300 import scaling
+
+    golden = os.path.join(os.path.dirname(__file__), "golden")
+    doc = json.load(open(os.path.join(golden, "mera_chi4_z2.json")))
+    cft = json.load(open(os.path.join(golden, "paper_values.json")))
+    top = doc["layers"][-1]
+    chi = top["chi_t"]
+    u = np.array(top["u"]).reshape((chi,) * 4)
+    w = np.array(top["w"]).reshape(chi, chi, chi)
+    got = scaling.scaling_dimensions(_cuda(u), _cuda(w), chi, k=8)[:6]
+    want = O.scaling_dimensions(u, w, 8)[:6]
+    np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-8)
+    d_id, d_sigma, d_eps = cft["ising_cft_scaling_dims"]["value"]
+    assert got[0] == pytest.approx(d_id, abs=1e-9)
+    assert abs(got[1] - d_sigma) < 0.003 and abs(got[2] - d_eps) < 0.002
+    assert np.all(np.abs(got[3:5] - cft["sigma_descendant"]["value"]) < 0.005) and got[5] > 1.5

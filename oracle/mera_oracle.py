@@ -170,6 +170,23 @@ def descend(rho, u, w):
     return 0.5 * (descend_case(rho, u, w, "even") + descend_case(rho, u, w, "odd"))
 
 
+def descend_rows(rho, u, w, rows):
+    """Selected rows of D(rho): for each ket triple (i, j, k) in `rows`, the
+    chi_b^3 entries D(rho)[i, j, k, :, :, :].  The networks of descend_case
+    with the ket legs i, j, k of the lower disentanglers held at one value,
+    so a row costs the whole map divided by those legs' dimensions (used to
+    check full-size results entry by entry)."""
+    out = []
+    for i, j, k in rows:
+        acc = 0.0
+        for case in ("even", "odd"):
+            specs = _KET_W + _KET_U[case] + _BRA_U[case] + _BRA_W + [_TOP]
+            ops = [w, w, w, u, u, u, u, w, w, w, rho]
+            acc = acc + _fixed(specs, ops, _OP, {"i": i, "j": j, "k": k})
+        out.append(0.5 * acc)
+    return np.stack(out)
+
+
 def energy(h, rho, u, w) -> float:
     """E(h, rho) = tr(A(h) rho) = sum A[p,q,r,s,t,v] rho[s,t,v,p,q,r]."""
     a = ascend(h, u, w)

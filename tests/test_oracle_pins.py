@@ -474,8 +474,9 @@ def test_converged_chi4_mera_reproduces_the_ising_cft():
 
 
 # --------------------------------------------------------------------------
-# Entry-wise helpers for full-size checks: ascend_rows, env_w_cols and
-# env_u_rows compute parts of the (pinned) maps with some legs held fixed.
+# Entry-wise helpers for full-size checks: ascend_rows, descend_rows,
+# env_w_cols and env_u_rows compute parts of the (pinned) maps with some legs
+# held fixed.
 # They must equal the corresponding parts of the whole maps.
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("chi_b,chi_t", [(3, 3), (2, 3), (4, 5), (3, 2)])
@@ -494,3 +495,7 @@ def test_row_and_column_helpers_equal_the_whole_maps(chi_b, chi_t):
     rows2 = [(0, 0), (chi_b - 1, 0), (1, chi_b - 1)]
     for k, r in enumerate(O.env_u_rows(h, rho, u, w, rows2)):
         assert np.abs(r - gu[rows2[k]]).max() < 1e-12
+    d = O.descend(rho, u, w)
+    rows_d = [(0, 0, 0), (chi_b - 1, 0, 1), (1, chi_b - 1, chi_b - 1)]
+    for k, r in enumerate(O.descend_rows(rho, u, w, rows_d)):
+        assert np.abs(r - d[rows_d[k]]).max() < 1e-12

@@ -40,6 +40,20 @@
  *                      parts (hi + mid + lo, 24 significant bits), the six
  *                      products whose parts' orders sum to at most 2, FP32
  *                      accumulation.
+ *     MERA_PREC_OZ3    tensor cores, fixed-point split (Ozaki, Ogita, Oishi
+ *                      and Rump, Numer. Algorithms 59, 2012): along the
+ *                      contraction index every row of an operand is cut into
+ *                      blocks of 256 elements sharing one exponent, and each
+ *                      entry into three BF16 slices of 9 bits each relative
+ *                      to the block's largest entry (~26 bits).  Within a
+ *                      block the leading-slice products sum exactly in FP32;
+ *                      block sums are accumulated as a pair of binary32
+ *                      values (~48 bits); the six slice products whose
+ *                      orders sum to at most 2 are kept.  Intermediates are
+ *                      stored as that pair and split again.  Map errors of
+ *                      ~1e-8 of the largest entry.
+ *     MERA_PREC_OZ4    the same with four slices (~35 bits) and ten
+ *                      products; map errors of ~1e-9.
  *   Polar updates, normalisation, traces and energies are binary64 always.
  */
 #ifndef MERA_GB300_H
@@ -65,6 +79,8 @@ typedef int mera_status;
 #define MERA_PREC_BF16 2
 #define MERA_PREC_BF16X3 3
 #define MERA_PREC_BF16X6 4
+#define MERA_PREC_OZ3 5
+#define MERA_PREC_OZ4 6
 
 /* Operation ids for mera_workspace_size / mera_plan_json. */
 #define MERA_OP_ASCEND 0
@@ -163,9 +179,17 @@ mera_status mera_env_w(const double* h, const double* rho, const double* u, cons
  * by the Newton-Schulz iteration X <- X (3 I - X^T X) / 2 from
  * X0 = env / ||env||_F, which converges to the polar factor for full column
  * rank.  Stops when ||X^T X - I||_F <= tol (tol <= 0 selects 1e-13 * sqrt(n))
- * or after max_iter steps (<= 0 selects 100); in the latter case returns
- * MERA_ENOTCONV with the last iterate written.  Synchronises the stream
- * to test convergence.  out [m*n] must not alias env.
+ * or after max_iter steps (<= 0 selects 100); in the latter case the last
+ * iterate is written and bit (1 << MERA_ENOTCONV) of the device status word
+ * is set (mera_device_status).  Asynchronous like every compute call: the
+ * steps run as a conditional while loop whose continuation the device
+ * decides, so the host never waits.  The first call with a given (env, out,
+ * ws, ws_bytes, m, n, max_iter, tol) in a CUDA context records and
+ * instantiates that loop (host work only, no synchronisation) and keeps it
+ * (at most 256 such instantiations, the least recently used one discarded);
+ * later calls with the same arguments launch it.  Inside a stream capture
+ * the loop is recorded into the caller's graph instead.  out [m*n] must not
+ * alias env.
  */
 mera_status mera_polar_update(const double* env, int m, int n, double* out, int max_iter,
                               double tol, void* ws, size_t ws_bytes, void* stream);
@@ -209,8 +233,9 @@ typedef struct {
  * finally *e_dev = (tr(h1 rho1) + shift) / 2, the energy per spin with the
  * new tensors.  Layer dimensions must chain: chi_t[k] == chi_b[k+1], and
  * the last layer has chi_b == chi_t.  h1_dev is [chi_b[0]^6] on the device.
- * Returns MERA_ENOTCONV if a polar update hit its iteration cap (the sweep
- * is still completed).
+ * Asynchronous on the stream (no host synchronisation).  A polar update that
+ * hits its iteration cap sets bit (1 << MERA_ENOTCONV) of the device status
+ * word; the sweep is still completed.
  */
 mera_status mera_sweep(mera_state* state, const double* h1_dev, double shift, int n_pow, int prec,
                        void* ws, size_t ws_bytes, double* e_dev, void* stream);
@@ -224,10 +249,10 @@ mera_status mera_sweep(mera_state* state, const double* h1_dev, double shift, in
  * lane: one host thread issues its members in index order, so they run one
  * after another and may share one scratch buffer (large enough for each of
  * them).  Lanes run concurrently: a pool of n_threads host threads issues
- * them, so that one MERA's host-side convergence checks do not hold back the
- * others.  Each MERA's result is exactly what mera_sweep gives for it alone.
- * Returns the most severe status of the batch (MERA_ENOTCONV if only polar
- * caps were hit); the error text names the MERA.  MERA_EINVAL, before any
+ * them, so that the launches of different lanes are issued in parallel.
+ * Each MERA's result is exactly what mera_sweep gives for it alone.
+ * Returns the most severe status of the batch; the error text names the
+ * MERA.  MERA_EINVAL, before any
  * work, if one scratch pointer is given with two different streams (only
  * identical pointers are detected; partly overlapping buffers are the
  * caller's error).
@@ -265,8 +290,8 @@ mera_status mera_batch_lanes(int n, int n_layers, const int* chi_b, const int* c
  * i.e. one gradient step of length eta along the Riemannian gradient of the
  * embedded metric, retracted to the manifold by the polar factor (computed
  * by the polar update's Newton-Schulz iteration).  out may alias X, not G.
- * Scratch: mera_stiefel_workspace_size(m, n).  MERA_ENOTCONV as for
- * mera_polar_update.
+ * Scratch: mera_stiefel_workspace_size(m, n).  Non-convergence of the
+ * retraction is reported as for mera_polar_update.
  *
  * mera_sweep_riemannian: mera_sweep with every tensor update replaced by
  * mera_stiefel_step(X, 2 Gamma, eta) (2 Gamma is the energy's gradient for
@@ -301,8 +326,8 @@ mera_status mera_flops(int op, int chi_b, int chi_t, double* flops);
  * Device-side failure word of the current device: bit (1 << MERA_ETIMEOUT)
  * is set when a bounded wait inside a tensor-core kernel gave up (the kernel
  * then skipped its remaining work and returned; its outputs are invalid);
- * bit (1 << MERA_ENOTCONV) when a polar update recorded in a graph (below)
- * did not converge within its step limit.
+ * bit (1 << MERA_ENOTCONV) when a polar update (a direct call or one
+ * recorded in a graph, below) did not converge within its step limit.
  * Synchronises with the device.  clear != 0 resets the word afterwards.
  */
 mera_status mera_device_status(int* status, int clear);
@@ -320,10 +345,10 @@ mera_status mera_device_status(int* status, int clear);
  * captured by address and must stay allocated (and hold the state to update)
  * until mera_graph_destroy.  Inside the recording every polar update is a
  * conditional while-loop node: Newton-Schulz steps repeat until the device
- * sees convergence (at most 100 steps, as in mera_polar_update), with no
- * host check; non-convergence is reported through bit MERA_ENOTCONV of
- * mera_device_status instead of a return status.  A replay gives
- * bit-identical results to mera_sweep on the same inputs.
+ * sees convergence (at most 100 steps), with no host check, exactly as a
+ * direct mera_polar_update runs it; non-convergence is reported through bit
+ * MERA_ENOTCONV of mera_device_status.  A replay gives bit-identical results
+ * to mera_sweep on the same inputs.
  * mera_graph_launch enqueues one replay on `stream` (any stream).
  */
 typedef struct mera_graph_s* mera_graph;

@@ -13,7 +13,8 @@ import os
 import threading
 
 __all__ = [
-    "MeraError", "MeraNotConverged", "PREC_F64", "PREC_TF32", "PREC_BF16", "PREC_BF16X3", "PREC_BF16X6", "PRECS",
+    "MeraError", "MeraNotConverged", "PREC_F64", "PREC_TF32", "PREC_BF16", "PREC_BF16X3", "PREC_BF16X6",
+    "PREC_OZ3", "PREC_OZ4", "PRECS",
     "OP_ASCEND", "OP_DESCEND", "OP_ENV_U", "OP_ENV_W", "OP_ENERGY", "OP_FIXED_POINT",
     "library", "library_path", "mera_version", "mera_workspace_size", "mera_ascend", "mera_descend",
     "mera_fixed_point_rho", "mera_env_u", "mera_env_w", "mera_polar_update", "mera_polar_workspace_size",
@@ -26,8 +27,9 @@ __all__ = [
     "mera_batch_lanes", "batch_resources", "mera_set_tile_width", "mera_tile_widths",
 ]
 
-PREC_F64, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3, 4
-PRECS = {"f64": PREC_F64, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x3": PREC_BF16X3, "bf16x6": PREC_BF16X6}
+PREC_F64, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_BF16X6, PREC_OZ3, PREC_OZ4 = 0, 1, 2, 3, 4, 5, 6
+PRECS = {"f64": PREC_F64, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x3": PREC_BF16X3, "bf16x6": PREC_BF16X6,
+         "oz3": PREC_OZ3, "oz4": PREC_OZ4}
 OP_ASCEND, OP_DESCEND, OP_ENV_U, OP_ENV_W, OP_ENERGY, OP_FIXED_POINT = 0, 1, 2, 3, 4, 5
 MAX_LAYERS = 8
 PROF_GEMM, PROF_GEMM_DOMINANT, PROF_PERMUTE = 0, 1, 2
@@ -460,8 +462,9 @@ def mera_gemm_test(prec, A, B, C, stream=None):
     eb = 8 if prec == PREC_F64 else (4 if prec == PREC_TF32 else 2)
     ld = (K * eb + 15) // 16 * 16 // eb
     pad = lambda x: (x + 255) // 256 * 256  # noqa: E731
-    planes = {PREC_BF16X3: 2, PREC_BF16X6: 3}.get(prec, 1)
-    ws = workspace(planes * (pad(M * ld * eb) + pad(N * ld * eb)), A.device)
+    planes = {PREC_BF16X3: 2, PREC_BF16X6: 3, PREC_OZ3: 3, PREC_OZ4: 4}.get(prec, 1)
+    raw = 2 * (pad(M * ld * 4) + pad(N * ld * 4)) if prec in (PREC_OZ3, PREC_OZ4) else 0
+    ws = workspace(planes * (pad(M * ld * eb) + pad(N * ld * eb)) + raw, A.device)
     p, n = _ws(ws)
     _check(library().mera_gemm_test(prec, _f64(A, M * K, "A"), _f64(B, N * K, "B"), M, N, K, _f64(C, M * N, "C"),
                                     p, n, _stream(stream)))

@@ -14,6 +14,7 @@
 #include <mutex>
 #include <set>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/mera.h"
@@ -114,7 +115,50 @@ bool chi_ok(int chi_b, int chi_t) {
   return chi_b >= 1 && chi_t >= 1 && chi_b <= MERA_MAX_CHI && chi_t <= MERA_MAX_CHI &&
          int64_t(chi_t) <= int64_t(chi_b) * chi_b;
 }
-bool prec_ok(int prec) { return prec >= MERA_PREC_F64 && prec <= MERA_PREC_BF16X6; }
+bool prec_ok(int prec) { return prec >= MERA_PREC_F64 && prec <= MERA_PREC_OZ4; }
+
+// Bytes of one element of a program buffer (raw buffers of the fixed-point
+// split modes hold binary32 planes).
+int64_t buf_elem_bytes(const Buffer& b, int prec) { return b.raw ? 4 : elem_bytes(prec); }
+
+// Tensor-core GEMM arguments of one program step; `out` is the caller's
+// output (root steps), `base` the workspace.
+TcGemmArgs tc_args(const GemmStep& g, const Program& dg, int prec, char* base, double* out) {
+  TcGemmArgs args;
+  args.prec = prec;
+  const int64_t eb = elem_bytes(prec);
+  args.A = base + dg.bufs[g.a_buf].offset + g.a_off * eb;
+  args.a_plane_bytes = dg.bufs[g.a_buf].plane_bytes;
+  args.lda = g.lda;
+  args.B = base + dg.bufs[g.b_buf].offset + g.b_off * eb;
+  args.b_plane_bytes = dg.bufs[g.b_buf].plane_bytes;
+  args.ldb = g.ldb;
+  args.M = g.M;
+  args.N = g.N;
+  args.K = g.K;
+  args.c_final = g.c_buf < 0;
+  if (g.c_buf >= 0) {
+    const Buffer& c = dg.bufs[g.c_buf];
+    const int64_t ce = buf_elem_bytes(c, prec);
+    args.C = base + c.offset + g.c_off * ce;
+    args.c_plane_elems = c.plane_bytes / ce;
+  } else {
+    args.C = out + g.c_off;
+    args.c_plane_elems = 0;
+  }
+  args.m_dst = g.m_dst;
+  args.n_dst = g.n_dst;
+  args.alpha = g.alpha;
+  args.accumulate = g.accumulate;
+  args.split = g.split;
+  args.bn = g.bn;
+  if (g.p_buf >= 0) {
+    const Buffer& p = dg.bufs[g.p_buf];
+    args.partial = reinterpret_cast<float*>(base + p.offset);
+    args.partial_plane = p.plane_bytes / 4;
+  }
+  return args;
+}
 
 int64_t ipow(int64_t b, int e) {
   int64_t r = 1;
@@ -149,11 +193,23 @@ mera_status run_program(const OpProgram& prog, const double* const inputs[4], do
       if (st.kind == 0) {
         const PermuteStep& p = st.p;
         const Buffer& b = dg.bufs[p.dst_buf];
-        if (p.skip || (reuse_resident && b.resident == 1)) continue;
-        const int64_t plane = b.plane_bytes / elem_bytes(prec);
+        if (p.skip || (reuse_resident && dg.bufs[p.op_buf].resident == 1)) continue;
+        const int64_t plane = b.plane_bytes / buf_elem_bytes(b, prec);
         ProfScope ps(stream, 1, 0, 0.0);
-        cudaError_t e = launch_permute(p, inputs[p.slot], ws + b.offset, plane, prec, stream);
+        cudaError_t e = launch_permute(p, inputs[p.slot], ws + b.offset, plane, b.raw ? PREC_RAW : prec, stream);
         if (e != cudaSuccess) return cuda_status(e, "permute");
+        continue;
+      }
+      if (st.kind == 2) {  // fixed-point split of a raw buffer into its operand
+        const SplitStep& x = st.x;
+        const Buffer& r = dg.bufs[x.raw_buf];
+        const Buffer& d = dg.bufs[x.dst_buf];
+        if (x.skip || (reuse_resident && d.resident == 1)) continue;
+        ProfScope ps(stream, 1, 0, 0.0);
+        cudaError_t e = launch_oz_split(reinterpret_cast<const float*>(ws + r.offset), r.plane_bytes / 4,
+                                        ws + d.offset, d.plane_bytes / elem_bytes(prec), x.rows, x.K, x.ld,
+                                        planes(prec), stream);
+        if (e != cudaSuccess) return cuda_status(e, "split");
         continue;
       }
       const GemmStep& g = st.g;
@@ -180,29 +236,7 @@ mera_status run_program(const OpProgram& prog, const double* const inputs[4], do
         cudaError_t e = launch_gemm_f64(args, stream);
         if (e != cudaSuccess) return cuda_status(e, "gemm_f64");
       } else {
-        TcGemmArgs args;
-        args.prec = prec;
-        const int64_t eb = elem_bytes(prec);
-        args.A = ws + a.offset + g.a_off * eb;
-        args.a_plane_bytes = a.plane_bytes;
-        args.lda = g.lda;
-        args.B = ws + b.offset + g.b_off * eb;
-        args.b_plane_bytes = b.plane_bytes;
-        args.ldb = g.ldb;
-        args.M = g.M;
-        args.N = g.N;
-        args.K = g.K;
-        args.c_final = g.c_buf < 0;
-        args.C = g.c_buf >= 0 ? static_cast<void*>(ws + dg.bufs[g.c_buf].offset + g.c_off * eb)
-                              : static_cast<void*>(out + g.c_off);
-        args.c_plane_elems = g.c_buf >= 0 ? dg.bufs[g.c_buf].plane_bytes / elem_bytes(prec) : 0;
-        args.m_dst = g.m_dst;
-        args.n_dst = g.n_dst;
-        args.alpha = g.alpha;
-        args.accumulate = g.accumulate;
-        args.split = g.split;
-        args.bn = g.bn;
-        args.partial = g.p_buf >= 0 ? reinterpret_cast<float*>(ws + dg.bufs[g.p_buf].offset) : nullptr;
+        const TcGemmArgs args = tc_args(g, dg, prec, ws, out);
         cudaError_t e = launch_gemm_tc(args, stream);
         if (e == cudaErrorNotSupported) return fail(MERA_EINVAL, "tensor-core GEMM unavailable for prec %d", prec);
         if (e != cudaSuccess) return cuda_status(e, "gemm_tc");
@@ -371,23 +405,12 @@ extern "C" mera_status mera_polar_workspace_size(int m, int n, size_t* bytes) {
   return MERA_OK;
 }
 
-extern "C" mera_status mera_polar_update(const double* env, int m, int n, double* out, int max_iter, double tol,
-                                         void* ws, size_t ws_bytes, void* stream) {
-  if (!env || !out || env == out) return fail(MERA_EINVAL, "bad env/out pointers");
-  if (m < 1 || n < 1 || m < n || m > 1 << 16) return fail(MERA_EINVAL, "polar needs m >= n >= 1 (m=%d n=%d)", m, n);
-  const size_t need = polar_bytes(m, n);
-  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(MERA_EINVAL, "workspace not 256-byte aligned");
-  if (!ws || ws_bytes < need) return fail(MERA_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // Inside a stream capture the host cannot look at the iteration state: the
-  // iteration is recorded as a conditional while-loop node whose body ends
-  // with a kernel that decides on the device whether to go on, and
-  // non-convergence goes to the device status word.
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return fail(MERA_ECUDA, "stream capture status");
-  const bool capturing = cap != cudaStreamCaptureStatusNone;
-  if (max_iter <= 0) max_iter = 100;
-  if (!(tol > 0)) tol = 1e-13 * std::sqrt(double(n));
+// Records the whole polar update on the capturing stream s: scaling, the
+// Newton-Schulz steps as a conditional while-loop node whose body ends with
+// a kernel that decides on the device whether to go on, the result chosen
+// on the device, and non-convergence set in the device status word.
+static mera_status polar_record(const double* env, int m, int n, double* out, int max_iter, double tol, void* ws,
+                                size_t ws_bytes, cudaStream_t s) {
   Arena ar{static_cast<char*>(ws), ws_bytes};
   double* X = reinterpret_cast<double*>(ar.take(size_t(m) * n * sizeof(double)));
   double* Xn = reinterpret_cast<double*>(ar.take(size_t(m) * n * sizeof(double)));
@@ -402,10 +425,7 @@ extern "C" mera_status mera_polar_update(const double* env, int m, int n, double
   col_1.n = 1; col_1.dim[0] = n; col_1.stride[0] = 1;
   row_m.n = 1; row_m.dim[0] = m; row_m.stride[0] = n;
   // Device-gated iterations: once the residual is below tol, one more step
-  // runs and every later kernel returns at once.  Without capture the host
-  // looks at the state only every kCheck steps, so the stream is not drained
-  // each step.
-  constexpr int kCheck = 4;
+  // runs and every later kernel returns at once.
   int* state = reinterpret_cast<int*>(scalars + 4);  // done, iterations, converged-after-this-step
   if ((e = cudaMemsetAsync(state, 0, 3 * sizeof(int), s)) != cudaSuccess) return cuda_status(e, "polar state");
   // G = x^T x (skipped once converged)
@@ -434,62 +454,147 @@ extern "C" mera_status mera_polar_update(const double* env, int m, int n, double
   };
   if ((e = gram(X, s)) != cudaSuccess) return cuda_status(e, "polar gemm");
   if ((e = launch_ns_prescale(G, X, m, n, scalars + 2, s)) != cudaSuccess) return cuda_status(e, "polar prescale");
-  int host_state[3] = {0, 0, 0};
-  double resid = 0.0;
-  if (!capturing) {
-    double* buf[2] = {X, Xn};
-    for (int it = 0; it < max_iter; ++it) {
-      if ((e = step(buf[it & 1], buf[(it + 1) & 1], s)) != cudaSuccess) return cuda_status(e, "polar step");
-      if ((it + 1) % kCheck == 0 || it + 1 == max_iter) {
-        if ((e = cudaMemcpyAsync(host_state, state, sizeof host_state, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(&resid, scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-          return cuda_status(e, "polar state copy");
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e, "polar sync");
-        if (host_state[0]) break;
-      }
-    }
-  } else {
-    // while (not converged and fewer than max_iter steps): X -> Xn -> X
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaGraph_t cg = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    const cudaGraphEdgeData* edges = nullptr;
-    size_t nd = 0;
-    if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, &edges, &nd)) != cudaSuccess)
-      return cuda_status(e, "capture info");
-    cudaGraphConditionalHandle h;
-    if ((e = cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
-      return cuda_status(e, "conditional handle");
-    cudaGraphNodeParams p = {};
-    p.type = cudaGraphNodeTypeConditional;
-    p.conditional.handle = h;
-    p.conditional.type = cudaGraphCondTypeWhile;
-    p.conditional.size = 1;
-    cudaGraphNode_t loop = nullptr;
-    if ((e = cudaGraphAddNode(&loop, cg, deps, edges, nd, &p)) != cudaSuccess) return cuda_status(e, "while node");
-    cudaGraph_t body = p.conditional.phGraph_out[0];
-    cudaStream_t bs = nullptr;
-    if ((e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking)) != cudaSuccess) return cuda_status(e, "body stream");
-    e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-    if (e == cudaSuccess) e = step(X, Xn, bs);
-    if (e == cudaSuccess) e = step(Xn, X, bs);
-    if (e == cudaSuccess) e = launch_ns_continue(state, h, max_iter, bs);
-    cudaGraph_t got = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(bs, &got);
-    cudaStreamDestroy(bs);
-    if (e != cudaSuccess || e2 != cudaSuccess) return cuda_status(e != cudaSuccess ? e : e2, "while body");
-    if ((e = cudaStreamUpdateCaptureDependencies(s, &loop, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
-        cudaSuccess)
-      return cuda_status(e, "capture dependencies");
-  }
+  // while (not converged and fewer than max_iter steps): X -> Xn -> X
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, &edges, &nd)) != cudaSuccess)
+    return cuda_status(e, "capture info");
+  cudaGraphConditionalHandle h;
+  if ((e = cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+    return cuda_status(e, "conditional handle");
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t loop = nullptr;
+  if ((e = cudaGraphAddNode(&loop, cg, deps, edges, nd, &p)) != cudaSuccess) return cuda_status(e, "while node");
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  cudaStream_t bs = nullptr;
+  if ((e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking)) != cudaSuccess) return cuda_status(e, "body stream");
+  e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) e = step(X, Xn, bs);
+  if (e == cudaSuccess) e = step(Xn, X, bs);
+  if (e == cudaSuccess) e = launch_ns_continue(state, h, max_iter, bs);
+  cudaGraph_t got = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(bs, &got);
+  cudaStreamDestroy(bs);
+  if (e != cudaSuccess || e2 != cudaSuccess) return cuda_status(e != cudaSuccess ? e : e2, "while body");
+  if ((e = cudaStreamUpdateCaptureDependencies(s, &loop, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+      cudaSuccess)
+    return cuda_status(e, "capture dependencies");
   e = launch_ns_output(X, Xn, state, out, int64_t(m) * n, s);  // -X of the last step, chosen on the device
   if (e != cudaSuccess) return cuda_status(e, "polar output");
-  if (capturing) {
-    if ((e = launch_report_notconv(state, s)) != cudaSuccess) return cuda_status(e, "polar report");
-    return MERA_OK;
+  if ((e = launch_report_notconv(state, s)) != cudaSuccess) return cuda_status(e, "polar report");
+  return MERA_OK;
+}
+
+namespace mera {
+namespace polar_detail {
+
+// Direct (uncaptured) polar updates launch an instantiated recording of the
+// same steps, so that the host never waits for the device.  Instantiations
+// are cached by everything the recording bakes in: the driver context, the
+// pointers, the sizes and the stopping rule.
+struct Key {
+  void* ctx;
+  const double* env;
+  double* out;
+  void* ws;
+  size_t ws_bytes;
+  int m, n, max_iter;
+  double tol;
+  bool operator<(const Key& o) const {
+    return std::tie(ctx, env, out, ws, ws_bytes, m, n, max_iter, tol) <
+           std::tie(o.ctx, o.env, o.out, o.ws, o.ws_bytes, o.m, o.n, o.max_iter, o.tol);
   }
-  const bool converged = host_state[0] && std::isfinite(resid) && resid <= tol;
-  if (!converged) return fail(MERA_ENOTCONV, "polar iteration did not converge (resid %.3e, tol %.3e)", resid, tol);
+};
+struct Entry {
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;  // kernels in the recording
+  unsigned long long used = 0;
+};
+constexpr size_t kMaxEntries = 256;
+std::mutex mu;
+std::map<Key, Entry> cache;
+unsigned long long tick = 0;
+
+void* current_context() {
+  using GetCtx = int (*)(void**);
+  static GetCtx fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<GetCtx>(p);
+  });
+  void* ctx = nullptr;
+  if (fn) fn(&ctx);
+  return ctx;
+}
+
+}  // namespace polar_detail
+}  // namespace mera
+
+extern "C" mera_status mera_polar_update(const double* env, int m, int n, double* out, int max_iter, double tol,
+                                         void* ws, size_t ws_bytes, void* stream) {
+  using namespace mera::polar_detail;
+  if (!env || !out || env == out) return fail(MERA_EINVAL, "bad env/out pointers");
+  if (m < 1 || n < 1 || m < n || m > 1 << 16) return fail(MERA_EINVAL, "polar needs m >= n >= 1 (m=%d n=%d)", m, n);
+  const size_t need = polar_bytes(m, n);
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(MERA_EINVAL, "workspace not 256-byte aligned");
+  if (!ws || ws_bytes < need) return fail(MERA_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (max_iter <= 0) max_iter = 100;
+  if (!(tol > 0)) tol = 1e-13 * std::sqrt(double(n));
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return fail(MERA_ECUDA, "stream capture status");
+  if (cap != cudaStreamCaptureStatusNone) return polar_record(env, m, n, out, max_iter, tol, ws, ws_bytes, s);
+  // Direct call: launch the cached instantiation of the recording (made on
+  // the first call with these arguments).
+  const Key key{current_context(), env, out, ws, ws_bytes, m, n, max_iter, tol};
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it == cache.end()) {
+    if (cache.size() >= kMaxEntries) {  // forget the least recently used one
+      auto old = cache.begin();
+      for (auto c = cache.begin(); c != cache.end(); ++c)
+        if (c->second.used < old->second.used) old = c;
+      cudaGraphExecDestroy(old->second.exec);  // freed once any launch in flight completes
+      cache.erase(old);
+    }
+    cudaStream_t ps = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_status(e, "polar recording stream");
+    const long long l0 = g_launch_count.load();
+    e = cudaStreamBeginCapture(ps, cudaStreamCaptureModeThreadLocal);
+    mera_status st = e == cudaSuccess ? polar_record(env, m, n, out, max_iter, tol, ws, ws_bytes, ps)
+                                      : cuda_status(e, "polar begin capture");
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(ps, &g) : cudaSuccess;
+    cudaStreamDestroy(ps);
+    const long long n_kernels = g_launch_count.load() - l0;
+    g_launch_count.fetch_sub(n_kernels);  // counted when launched
+    if (st != MERA_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e2 != cudaSuccess || !g) return cuda_status(e2 == cudaSuccess ? cudaErrorUnknown : e2, "polar end capture");
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_status(e, "polar instantiate");
+    it = cache.emplace(key, Entry{x, n_kernels, 0}).first;
+  }
+  it->second.used = ++tick;
+  const cudaError_t e = cudaGraphLaunch(it->second.exec, s);
+  if (e != cudaSuccess) return cuda_status(e, "polar launch");
+  count_launch(it->second.launches);
   return MERA_OK;
 }
 
@@ -651,21 +756,18 @@ static mera_status sweep_impl(mera_state* S, const double* h1, double shift, int
   double* env = reinterpret_cast<double*>(base + L.env_off);
   const double* rho_above = S->rho_star;
   int ping = 0;
-  bool notconv = false;
   for (int t = n - 1; t >= 0; --t) {
     const int cb = S->chi_b[t], ct = S->chi_t[t];
     st = mera_env_u(hs[t], rho_above, S->u[t], S->w[t], cb, ct, env, prec, mws, mb, stream);
     if (st != MERA_OK) return st;
     st = update ? mera_stiefel_step(S->u[t], env, cb * cb, cb * cb, 2.0 * eta, S->u[t], mws, mb, stream)
                 : mera_polar_update(env, cb * cb, cb * cb, S->u[t], 0, 0.0, mws, mb, stream);
-    if (st == MERA_ENOTCONV) notconv = true;
-    else if (st != MERA_OK) return st;
+    if (st != MERA_OK) return st;
     st = mera_env_w(hs[t], rho_above, S->u[t], S->w[t], cb, ct, env, prec, mws, mb, stream);
     if (st != MERA_OK) return st;
     st = update ? mera_stiefel_step(S->w[t], env, cb * cb, ct, 2.0 * eta, S->w[t], mws, mb, stream)
                 : mera_polar_update(env, cb * cb, ct, S->w[t], 0, 0.0, mws, mb, stream);
-    if (st == MERA_ENOTCONV) notconv = true;
-    else if (st != MERA_OK) return st;
+    if (st != MERA_OK) return st;
     if (t > 0 && t < n - 1) {  // rho* sits on top of the last transitional layer
       double* dst = reinterpret_cast<double*>(base + L.rho_off[ping]);
       ping ^= 1;
@@ -680,10 +782,7 @@ static mera_status sweep_impl(mera_state* S, const double* h1, double shift, int
   if (st != MERA_OK) return st;
   count_launch();
   energy_per_spin_kernel<<<1, 1, 0, s>>>(etmp, shift, e_dev);
-  st = cuda_status(cudaGetLastError(), "energy per spin");
-  if (st != MERA_OK) return st;
-  if (notconv) return fail(MERA_ENOTCONV, "a polar update hit its iteration cap");
-  return MERA_OK;
+  return cuda_status(cudaGetLastError(), "energy per spin");
 }
 
 extern "C" mera_status mera_sweep(mera_state* S, const double* h1, double shift, int n_pow, int prec, void* ws,
@@ -829,12 +928,16 @@ extern "C" mera_status mera_gemm_test(int prec, const double* A, const double* B
   const int64_t eb = elem_bytes(prec), np = planes(prec);
   const int64_t ld = (int64_t(K) * eb + 15) / 16 * 16 / eb;
   const size_t pa = align_up(size_t(M) * ld * eb), pb = align_up(size_t(N) * ld * eb);
-  const size_t need = np * (pa + pb);
+  // fixed-point split modes: raw hi + lo binary32 planes of both operands first
+  const size_t ra = is_oz(prec) ? align_up(size_t(M) * ld * 4) : 0, rb = is_oz(prec) ? align_up(size_t(N) * ld * 4) : 0;
+  const size_t need = np * (pa + pb) + 2 * (ra + rb);
   if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(MERA_EINVAL, "workspace not 256-byte aligned");
   if (!ws || ws_bytes < need) return fail(MERA_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char* wa = static_cast<char*>(ws);
   char* wb = wa + np * pa;
+  char* wra = wb + np * pb;
+  char* wrb = wra + 2 * ra;
   // operands: A row-major M x K, B row-major N x K, copied to padded pitch
   PermuteStep pa_step, pb_step;
   pa_step.rows = M; pa_step.cols = K; pa_step.ld = ld;
@@ -842,8 +945,18 @@ extern "C" mera_status mera_gemm_test(int prec, const double* A, const double* B
   pa_step.col_src.n = 1; pa_step.col_src.dim[0] = K; pa_step.col_src.stride[0] = 1;
   pb_step = pa_step;
   pb_step.rows = N; pb_step.row_src.dim[0] = N;
-  cudaError_t e = launch_permute(pa_step, A, wa, int64_t(pa / eb), prec, s);
-  if (e == cudaSuccess) e = launch_permute(pb_step, B, wb, int64_t(pb / eb), prec, s);
+  cudaError_t e = cudaSuccess;
+  if (is_oz(prec)) {
+    e = launch_permute(pa_step, A, wra, int64_t(ra / 4), PREC_RAW, s);
+    if (e == cudaSuccess) e = launch_permute(pb_step, B, wrb, int64_t(rb / 4), PREC_RAW, s);
+    if (e == cudaSuccess)
+      e = launch_oz_split(reinterpret_cast<const float*>(wra), int64_t(ra / 4), wa, int64_t(pa / eb), M, K, ld, int(np), s);
+    if (e == cudaSuccess)
+      e = launch_oz_split(reinterpret_cast<const float*>(wrb), int64_t(rb / 4), wb, int64_t(pb / eb), N, K, ld, int(np), s);
+  } else {
+    e = launch_permute(pa_step, A, wa, int64_t(pa / eb), prec, s);
+    if (e == cudaSuccess) e = launch_permute(pb_step, B, wb, int64_t(pb / eb), prec, s);
+  }
   if (e != cudaSuccess) return cuda_status(e, "gemm test operands");
   LegMap md, nd;
   md.n = 1; md.dim[0] = M; md.stride[0] = N;
@@ -1036,7 +1149,7 @@ extern "C" mera_status mera_autotune(int op, int chi_b, int chi_t, int prec, dou
       const int cf = g.c_buf < 0 ? 1 : 0;
       if (g.N <= 64 || g.split > 1 || !seen.insert({g.M, g.N, g.K, cf}).second) continue;
       std::vector<int> cands = {128, 64};
-      if (g.N > 128 && prec != PREC_BF16X6) cands.insert(cands.begin(), 256);
+      if (g.N > 128 && prec != PREC_BF16X6 && !is_oz(prec)) cands.insert(cands.begin(), 256);
       if (g.N <= 128) cands = {128, 64};
       // the planner's own choice wins unless another width is clearly (3 %)
       // faster: single-step timings on scratch data carry noise
@@ -1045,23 +1158,11 @@ extern "C" mera_status mera_autotune(int op, int chi_b, int chi_t, int prec, dou
       float best_ms = 0.0f, heur_ms = 0.0f;
       for (int bn : cands) {
         if (tc_split_k(prec, g.M, g.N, g.K, bn) > 1) continue;  // timed only without a K split
-        TcGemmArgs a;
-        const int64_t eb = elem_bytes(prec);
-        a.prec = prec;
-        a.A = base + dg.bufs[g.a_buf].offset + g.a_off * eb;
-        a.a_plane_bytes = dg.bufs[g.a_buf].plane_bytes;
-        a.lda = g.lda;
-        a.B = base + dg.bufs[g.b_buf].offset + g.b_off * eb;
-        a.b_plane_bytes = dg.bufs[g.b_buf].plane_bytes;
-        a.ldb = g.ldb;
-        a.M = g.M; a.N = g.N; a.K = g.K;
-        a.c_final = cf != 0;
-        a.C = cf ? static_cast<void*>(out_scratch + g.c_off)
-                 : static_cast<void*>(base + dg.bufs[g.c_buf].offset + g.c_off * eb);
-        a.c_plane_elems = cf ? 0 : dg.bufs[g.c_buf].plane_bytes / eb;
-        a.m_dst = g.m_dst; a.n_dst = g.n_dst;
-        a.alpha = g.alpha; a.accumulate = 0;
-        a.split = 1; a.bn = bn;
+        TcGemmArgs a = tc_args(g, dg, prec, base, out_scratch);
+        a.accumulate = 0;
+        a.split = 1;
+        a.partial = nullptr;
+        a.bn = bn;
         cudaError_t e = launch_gemm_tc(a, s);  // warm
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
         for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = launch_gemm_tc(a, s);
@@ -1103,7 +1204,7 @@ extern "C" mera_status mera_set_tile_width(int prec, long long M, long long N, l
   if (!prec_ok(prec) || prec == PREC_F64) return fail(MERA_EINVAL, "tile widths apply to the tensor-core modes");
   if (M < 1 || N < 1 || K < 1 || (c_final != 0 && c_final != 1)) return fail(MERA_EINVAL, "bad GEMM shape");
   if (bn != 0) {
-    const bool ok = N > 128  ? (bn == 128 || bn == 64 || (bn == 256 && prec != PREC_BF16X6))
+    const bool ok = N > 128  ? (bn == 128 || bn == 64 || (bn == 256 && prec != PREC_BF16X6 && !is_oz(prec)))
                     : N > 64 ? (bn == 128 || bn == 64)
                              : false;
     if (!ok) return fail(MERA_EINVAL, "width %d is not an autotuner candidate for N = %lld", bn, N);

@@ -113,4 +113,23 @@ struct OperandStore<PREC_BF16X6> {
   }
 };
 
+// Fixed-point split modes: inputs are first stored as an unevaluated pair
+// hi + lo of binary32 values (hi = x rounded to binary32, lo = the rest
+// rounded; ~48 significant bits) in two planes, then split per block
+// (oz_split.cu).
+template <>
+struct OperandStore<PREC_RAW> {
+  using T = float;
+  __device__ __forceinline__ static void store(void* base, int64_t off, int64_t plane, double v) {
+    const float hi = __double2float_rn(v);
+    const float lo = __double2float_rn(v - double(hi));
+    static_cast<float*>(base)[off] = hi;
+    static_cast<float*>(base)[off + plane] = lo;
+  }
+  __device__ __forceinline__ static void store_f(void* base, int64_t off, int64_t plane, float f) {
+    static_cast<float*>(base)[off] = f;
+    static_cast<float*>(base)[off + plane] = 0.0f;
+  }
+};
+
 }  // namespace mera

@@ -14,9 +14,17 @@ namespace mera {
 extern std::atomic<long long> g_launch_count;
 inline void count_launch(long long n = 1) { g_launch_count.fetch_add(n, std::memory_order_relaxed); }
 
-// Input tensor -> operand layout, cast to the operand precision.
+// Input tensor -> operand layout, cast to the operand precision (in the
+// fixed-point split modes: to the raw hi + lo binary32 planes).
 cudaError_t launch_permute(const PermuteStep& p, const double* src, void* dst, int64_t plane_elems,
                            int prec, cudaStream_t stream);
+
+// Fixed-point split modes: raw hi + lo binary32 planes (rows x ld, the lo
+// plane raw_plane floats after the hi plane) -> `slices` BF16 planes of the
+// operand (dst_plane elements apart), one exponent per row and block of
+// kOzBlockK elements along K.  Columns K..ld-1 are not touched.
+cudaError_t launch_oz_split(const float* raw, int64_t raw_plane, void* dst, int64_t dst_plane, int64_t rows,
+                            int64_t K, int64_t ld, int slices, cudaStream_t stream);
 
 // FP64 GEMM with a scattered epilogue:
 //   C[m_dst(m) + n_dst(n)] (+)= alpha * sum_k A[m*a_m + k*a_k] * B[n*b_n + k*b_k]

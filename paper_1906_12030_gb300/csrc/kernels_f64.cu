@@ -216,6 +216,9 @@ cudaError_t launch_permute(const PermuteStep& st, const double* src, void* dst, 
     case PREC_BF16: MERA_PERMUTE_LAUNCH(PREC_BF16) break;
     case PREC_BF16X3: MERA_PERMUTE_LAUNCH(PREC_BF16X3) break;
     case PREC_BF16X6: MERA_PERMUTE_LAUNCH(PREC_BF16X6) break;
+    case PREC_OZ3:
+    case PREC_OZ4:  // into the raw hi + lo planes; the split step follows
+    case PREC_RAW: MERA_PERMUTE_LAUNCH(PREC_RAW) break;
     default: return cudaErrorInvalidValue;
   }
 #undef MERA_PERMUTE_LAUNCH

@@ -23,7 +23,9 @@ int elem_bytes(int prec) {
   }
 }
 int tc_block_n(int prec, int64_t N) {
-  if (N > 128) return prec == PREC_BF16X6 ? 128 : 256;
+  // the fixed-point split modes keep two accumulators per buffer in tensor
+  // memory (4 x width columns of 512): 128 at most
+  if (N > 128) return (prec == PREC_BF16X6 || is_oz(prec)) ? 128 : 256;
   if (N > 64) return 128;
   if (N > 16) return 64;
   return 16;
@@ -34,6 +36,16 @@ int tc_split_k(int prec, int64_t M, int64_t N, int64_t K, int bn_in) {
   constexpr int64_t kSMs = 152;
   const int64_t bn = bn_in > 0 ? bn_in : tc_block_n(prec, N);
   const int64_t tiles = ((M + 127) / 128) * ((N + bn - 1) / bn);
+  if (is_oz(prec)) {
+    // splits hold whole blocks of kOzBlockK (the kernel's exact-sum unit);
+    // enough splits for about two waves, at least two blocks each
+    const int64_t nblk = (K + kOzBlockK - 1) / kOzBlockK;
+    if (tiles >= kSMs || nblk < 4) return 1;
+    const int64_t want = std::min<int64_t>((2 * kSMs + tiles - 1) / tiles, nblk / 2);
+    if (want < 2) return 1;
+    const int64_t per = (nblk + want - 1) / want;  // blocks per split
+    return int((nblk + per - 1) / per);             // splits actually non-empty
+  }
   const int64_t bk = 128 / elem_bytes(prec);  // K per stage of the GEMM kernel
   const int64_t num_k = (K + bk - 1) / bk;
   if (tiles >= kSMs || num_k < 8) return 1;
@@ -57,7 +69,19 @@ int tc_split_k(int prec, int64_t M, int64_t N, int64_t K, int bn_in) {
   return int(best);
 }
 
-int planes(int prec) { return prec == PREC_BF16X3 ? 2 : (prec == PREC_BF16X6 ? 3 : 1); }
+int planes(int prec) {
+  switch (prec) {
+    case PREC_BF16X3: return 2;
+    case PREC_BF16X6: return 3;
+    case PREC_OZ3: return 3;
+    case PREC_OZ4: return 4;
+    default: return 1;
+  }
+}
+
+// Bytes per element of an operand buffer, counting the raw (hi, lo binary32)
+// buffer that the fixed-point split modes write before splitting.
+double operand_elem_bytes(int prec) { return double(elem_bytes(prec) * planes(prec)) + (is_oz(prec) ? 8.0 : 0.0); }
 
 namespace {
 
@@ -254,6 +278,8 @@ struct Builder {
   // elements) and the operand buffer it lives in.
   std::vector<std::map<int, int64_t>> dst_stride;
   std::vector<int> buf_of;
+  std::vector<int> raw_of;      // fixed-point split modes: raw buffer of each node's operand
+  std::vector<int64_t> k_of;    // K of the GEMM that reads each node's operand
   // GEMM info per internal node
   struct G {
     int a = -1, b = -1;
@@ -336,7 +362,7 @@ struct Builder {
     gs.K = prod(gi.klegs);
     gs.lda = prog.bufs[gs.a_buf].ld;
     gs.ldb = prog.bufs[gs.b_buf].ld;
-    gs.c_buf = (i == tr.root) ? -1 : buf_of[i];
+    gs.c_buf = (i == tr.root) ? -1 : (is_oz(prec) ? raw_of[i] : buf_of[i]);
     if (i != tr.root && is_static[i]) {
       gs.stat = 1;
       prog.bufs[buf_of[i]].resident = 1;
@@ -371,7 +397,7 @@ struct Builder {
       pb.rows = int64_t(gs.split) * gs.N;
       pb.ld = gs.M;
       pb.plane_bytes = round_up(pb.rows * pb.ld * 4, 256);
-      pb.bytes = pb.plane_bytes;
+      pb.bytes = pb.plane_bytes * (is_oz(prec) ? 2 : 1);  // hi, lo planes in the split modes
       prog.bufs.push_back(pb);
       gs.p_buf = int(prog.bufs.size()) - 1;
       first_use.push_back(-1);
@@ -404,6 +430,25 @@ struct Builder {
     }
   }
 
+  // Fixed-point split modes: node i's raw buffer -> its operand buffer, once
+  // the raw buffer is complete.
+  void emit_split(int i, std::vector<int>& first_use, std::vector<int>& last_use) {
+    if (!is_oz(prec) || i == tr.root) return;
+    Step s;
+    s.kind = 2;
+    SplitStep& x = s.x;
+    x.raw_buf = raw_of[i];
+    x.dst_buf = buf_of[i];
+    x.rows = prog.bufs[x.dst_buf].rows;
+    x.ld = prog.bufs[x.dst_buf].ld;
+    x.K = k_of[i];
+    prog.steps.push_back(s);
+    const int si = int(prog.steps.size()) - 1;
+    if (last_use[x.raw_buf] < si) last_use[x.raw_buf] = si;
+    if (first_use[x.dst_buf] < 0) first_use[x.dst_buf] = si;
+    if (last_use[x.dst_buf] < si) last_use[x.dst_buf] = si;
+  }
+
   bool build() {
     const int n = int(dg.tensors.size());
     std::vector<uint64_t> tmask(n, 0);
@@ -424,6 +469,8 @@ struct Builder {
     }
     dst_stride.assign(nn, {});
     buf_of.assign(nn, -1);
+    raw_of.assign(nn, -1);
+    k_of.assign(nn, 0);
     g.assign(nn, {});
     // GEMM roles (bottom-up information only depends on leg sets).
     for (size_t i = 0; i < nn; ++i) {
@@ -450,7 +497,7 @@ struct Builder {
       for (int c : {g[i].a, g[i].b}) {
         const Node& cn = tr.nodes[c];
         if (cn.tensor >= 0 || popcount64(cn.legs) != 7) continue;
-        const double bytes = size_of(cn.legs, dim) * elem_bytes(prec) * planes(prec);
+        const double bytes = size_of(cn.legs, dim) * operand_elem_bytes(prec);
         if (bytes <= double(slice_threshold)) continue;
         const uint64_t K2 = tr.nodes[g[i].a].legs & tr.nodes[g[i].b].legs;
         int best = -1;
@@ -557,6 +604,15 @@ struct Builder {
         b.bytes = b.plane_bytes * planes(prec);
         prog.bufs.push_back(b);
         buf_of[c] = int(prog.bufs.size()) - 1;
+        k_of[c] = Kn;
+        if (is_oz(prec)) {  // hi, lo binary32 planes in the same layout, split afterwards
+          Buffer r = b;
+          r.raw = 1;
+          r.plane_bytes = round_up(b.rows * ld * 4, 256);
+          r.bytes = 2 * r.plane_bytes;
+          prog.bufs.push_back(r);
+          raw_of[c] = int(prog.bufs.size()) - 1;
+        }
       }
     }
     // Emit steps in post-order (children first).
@@ -573,10 +629,11 @@ struct Builder {
         s.kind = 0;
         PermuteStep& p = s.p;
         p.slot = ts.slot;
-        p.dst_buf = buf_of[i];
+        p.op_buf = buf_of[i];
+        p.dst_buf = is_oz(prec) ? raw_of[i] : buf_of[i];
         // which legs are rows vs cols of the destination: decided by strides
         // (cols = legs with stride < ld).
-        const Buffer& b = prog.bufs[p.dst_buf];
+        const Buffer& b = prog.bufs[p.op_buf];
         std::vector<std::pair<int64_t, int>> legs;  // (dst stride, label)
         for (const char* c = ts.legs; *c; ++c) legs.push_back({dst_stride[i].at(label_id(*c)), label_id(*c)});
         std::sort(legs.begin(), legs.end(), [](auto& x, auto& y) { return x.first > y.first; });
@@ -601,22 +658,26 @@ struct Builder {
         const int si = int(prog.steps.size()) - 1;
         first_use[p.dst_buf] = si;
         if (ts.slot == SLOT_U || ts.slot == SLOT_W)
-          prog.bufs[p.dst_buf].resident = 1;
+          prog.bufs[p.op_buf].resident = 1;
         else if (shared && shared->count(permute_key(p)))
-          prog.bufs[p.dst_buf].resident = 2;
+          prog.bufs[p.op_buf].resident = 2;
+        emit_split(i, first_use, last_use);
         continue;
       }
       if (deferred[i]) continue;  // emitted inside its consumer's slice loop
       if (slice_leg[i] < 0) {
         emit_gemm(i, -1, 0, 1, first_use, last_use);
+        emit_split(i, first_use, last_use);
         continue;
       }
       const int l = slice_leg[i];
       const int64_t bl = slice_block[i];
       for (int64_t v = 0; v < dim[l] / bl; ++v) {
         emit_gemm(sliced_child[i], l, v, bl, first_use, last_use);
+        emit_split(sliced_child[i], first_use, last_use);
         emit_gemm(i, l, v, bl, first_use, last_use);
       }
+      emit_split(i, first_use, last_use);  // every slice of i's output written
     }
     double fmax = 0.0;
     for (const Step& st : prog.steps)
@@ -677,7 +738,7 @@ std::map<std::tuple<int, int64_t, int64_t, int64_t, int>, int> g_tuned;  // (pre
 
 const OpProgram* get_program(int op, int chi_b, int chi_t, int prec) {
   if (op < OP_ASCEND || op > OP_ENV_W) return nullptr;
-  if (prec < PREC_F64 || prec > PREC_BF16X6) return nullptr;
+  if (prec < PREC_F64 || prec > PREC_LAST) return nullptr;
   if (chi_b < 1 || chi_t < 1 || chi_b > 64 || chi_t > 64) return nullptr;
   if (chi_t > chi_b * chi_b) return nullptr;
   std::lock_guard<std::mutex> lk(g_mu);
@@ -713,7 +774,7 @@ const OpProgram* get_program(int op, int chi_b, int chi_t, int prec) {
         if (st.kind == 0 && (st.p.slot == SLOT_OP || st.p.slot == SLOT_RHO)) {
           const std::string k = permute_key(st.p);
           if (count[k]++ == 0) order.push_back(k);
-          bytes[k] = pg.bufs[st.p.dst_buf].bytes;
+          bytes[k] = pg.bufs[st.p.op_buf].bytes;
         }
     std::set<std::string> shared;
     int64_t budget = int64_t(4) << 30;
@@ -735,16 +796,20 @@ const OpProgram* get_program(int op, int chi_b, int chi_t, int prec) {
     std::map<std::string, int64_t> made;  // key -> offset
     for (Program& pg : prog->diagrams) {
       std::vector<char> placed(pg.bufs.size(), 0);
-      for (Step& st : pg.steps) {
+      for (size_t si = 0; si < pg.steps.size(); ++si) {
+        Step& st = pg.steps[si];
         if (st.kind != 0) continue;
-        Buffer& bf = pg.bufs[st.p.dst_buf];
+        Buffer& bf = pg.bufs[st.p.op_buf];
         if (!bf.resident) continue;
-        placed[size_t(st.p.dst_buf)] = 1;
+        placed[size_t(st.p.op_buf)] = 1;
         const std::string k = permute_key(st.p);
         auto it = made.find(k);
         if (it != made.end()) {
           bf.offset = it->second;
           st.p.skip = 1;
+          // the split of that copy (fixed-point split modes) is skipped with it
+          if (si + 1 < pg.steps.size() && pg.steps[si + 1].kind == 2 && pg.steps[si + 1].x.dst_buf == st.p.op_buf)
+            pg.steps[si + 1].x.skip = 1;
         } else {
           bf.offset = int64_t(res_base);
           made[k] = bf.offset;
@@ -846,13 +911,19 @@ std::string program_json(const OpProgram& prog, int op, int chi_b, int chi_t, in
     for (size_t b = 0; b < p.bufs.size(); ++b)
       o << (b ? "," : "") << "{\"rows\":" << p.bufs[b].rows << ",\"ld\":" << p.bufs[b].ld
         << ",\"offset\":" << p.bufs[b].offset << ",\"bytes\":" << p.bufs[b].bytes
+        << ",\"plane_bytes\":" << p.bufs[b].plane_bytes << ",\"raw\":" << p.bufs[b].raw
         << ",\"resident\":" << p.bufs[b].resident << "}";
     o << "],\"steps\":[";
     for (size_t s = 0; s < p.steps.size(); ++s) {
       const Step& st = p.steps[s];
       o << (s ? "," : "");
-      if (st.kind == 0) {
+      if (st.kind == 2) {
+        o << "{\"kind\":\"split\",\"raw_buf\":" << st.x.raw_buf << ",\"dst_buf\":" << st.x.dst_buf
+          << ",\"rows\":" << st.x.rows << ",\"K\":" << st.x.K << ",\"ld\":" << st.x.ld << ",\"skip\":" << st.x.skip
+          << "}";
+      } else if (st.kind == 0) {
         o << "{\"kind\":\"permute\",\"slot\":" << st.p.slot << ",\"dst_buf\":" << st.p.dst_buf
+          << ",\"op_buf\":" << st.p.op_buf
           << ",\"rows\":" << st.p.rows << ",\"cols\":" << st.p.cols << ",\"ld\":" << st.p.ld
           << ",\"skip\":" << st.p.skip << ",\"row_src\":";
         lm(st.p.row_src);

@@ -17,7 +17,23 @@
 
 namespace mera {
 
-enum Prec : int { PREC_F64 = 0, PREC_TF32 = 1, PREC_BF16 = 2, PREC_BF16X3 = 3, PREC_BF16X6 = 4 };
+enum Prec : int {
+  PREC_F64 = 0,
+  PREC_TF32 = 1,
+  PREC_BF16 = 2,
+  PREC_BF16X3 = 3,
+  PREC_BF16X6 = 4,
+  PREC_OZ3 = 5,  // fixed-point split into 3 BF16 slices per 256-element block of K, exact block sums
+  PREC_OZ4 = 6,  // the same with 4 slices
+  PREC_LAST = PREC_OZ4,
+  // Not a mode: the storage format that the fixed-point split modes write
+  // first (an unevaluated pair hi + lo of binary32 planes), before the split.
+  PREC_RAW = 100
+};
+inline bool is_oz(int prec) { return prec == PREC_OZ3 || prec == PREC_OZ4; }
+// K elements over which a fixed-point split shares one exponent per row; the
+// GEMM sums the leading slice products of such a block exactly in FP32.
+constexpr int kOzBlockK = 256;
 enum Slot : int { SLOT_OP = 0, SLOT_RHO = 1, SLOT_U = 2, SLOT_W = 3 };
 enum Op : int { OP_ASCEND = 0, OP_DESCEND = 1, OP_ENV_U = 2, OP_ENV_W = 3 };
 
@@ -35,7 +51,8 @@ struct LegMap {
 // dst[r * ld + c] = src[row_src(r) + col_src(c)],  r < rows, c < cols.
 struct PermuteStep {
   int slot = 0;
-  int dst_buf = 0;
+  int dst_buf = 0;     // the operand buffer, or (fixed-point split modes) its raw buffer
+  int op_buf = 0;      // the operand buffer (== dst_buf unless a split step follows)
   int64_t rows = 0, cols = 0, ld = 0;
   int skip = 0;  // an earlier step of the same call already made this copy
   LegMap row_src, col_src;
@@ -62,10 +79,20 @@ struct GemmStep {
   std::string label;  // e.g. "aceiq*CDcdil->ADadelq" for inspection
 };
 
+// Fixed-point split modes: raw (hi + lo binary32 planes, written by a
+// permute or GEMM step) -> S BF16 slice planes of the operand buffer, the
+// exponent shared by each row's blocks of kOzBlockK elements along K.
+struct SplitStep {
+  int raw_buf = 0, dst_buf = 0;
+  int64_t rows = 0, K = 0, ld = 0;
+  int skip = 0;  // mirrors the skip of the permute step it follows
+};
+
 struct Step {
-  int kind = 0;  // 0 permute, 1 gemm
+  int kind = 0;  // 0 permute, 1 gemm, 2 split (fixed-point split modes)
   PermuteStep p;
   GemmStep g;
+  SplitStep x;
 };
 
 struct Buffer {
@@ -73,6 +100,7 @@ struct Buffer {
   int64_t offset = 0;         // byte offset in the workspace
   int64_t plane_bytes = 0;    // bytes of one plane (BF16X3 keeps hi, then lo)
   int64_t bytes = 0;          // plane_bytes * planes
+  int raw = 0;                // 1: raw buffer of a fixed-point split mode (hi, lo binary32 planes)
   int resident = 0;           // kept for the whole call, outside the transient arena:
                               // 1 copy of a disentangler/isometry (a later call with the
                               // same u, w may reuse it), 2 copy of h or rho that several
@@ -114,7 +142,7 @@ void clear_tuned_tiles();
 int tuned_tile_count();
 // Every recorded width as (prec, M, N, K, c_final, width), in key order.
 std::vector<std::vector<int64_t>> tuned_tiles();
-int planes(int prec);       // 2 for BF16X3 (hi, lo), 3 for BF16X6 (hi, mid, lo), else 1
+int planes(int prec);       // 2 for BF16X3 (hi, lo), 3 for BF16X6 (hi, mid, lo), 3 / 4 for OZ3 / OZ4, else 1
 
 // Builds (and caches) the program; thread safe.  Returns nullptr on bad input.
 const OpProgram* get_program(int op, int chi_b, int chi_t, int prec);

@@ -165,9 +165,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 }
 
 // Operand tensor maps, one per plane (hi, lo / hi, mid, lo for split modes).
+constexpr int kMaxPlanes = 4;
 struct TMaps {
-  CUtensorMap a[3];
-  CUtensorMap b[3];
+  CUtensorMap a[kMaxPlanes];
+  CUtensorMap b[kMaxPlanes];
 };
 
 struct Epilogue {
@@ -181,6 +182,7 @@ struct Epilogue {
   int split;        // K split: work item t covers output tile t % tiles and k-range t / tiles
   int kc;           // k-blocks per split
   float* partial;   // split > 1: raw FP32 partials [split][N][M], summed by splitk_reduce_kernel
+  int64_t p_plane;  // fixed-point split modes: floats from the hi to the lo plane of the partials
   int off32;        // every column offset n_dst(n) is below 2^31
   int alpha_exp;    // alpha == 2^alpha_exp exactly (alpha_pow2 set)
   int alpha_pow2;
@@ -562,6 +564,8 @@ __global__ void __launch_bounds__(256) splitk_reduce_kernel(const __grid_constan
   }
 }
 
+#include "oz_gemm.cuh"
+
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
@@ -608,7 +612,7 @@ cudaError_t launch_cfg(const TcGemmArgs& a, cudaStream_t stream) {
   TMaps tm;
   const char* A = static_cast<const char*>(a.A);
   const char* B = static_cast<const char*>(a.B);
-  for (int pl = 0; pl < 3; ++pl) {
+  for (int pl = 0; pl < kMaxPlanes; ++pl) {
     const int q = pl < C::kPlanes ? pl : 0;  // unused slots repeat plane 0
     if (!encode_operand(&tm.a[pl], A + q * a.a_plane_bytes, PREC, a.M, a.K, a.lda, kBM, C::kSlab))
       return cudaErrorInvalidValue;
@@ -637,6 +641,7 @@ cudaError_t launch_cfg(const TcGemmArgs& a, cudaStream_t stream) {
   ep.split = split;
   ep.kc = int((num_k + split - 1) / split);
   ep.partial = a.partial;
+  ep.p_plane = 0;
   {
     // largest column offset, to allow 32-bit column offsets (the row
     // offset stays 64-bit)
@@ -668,6 +673,94 @@ cudaError_t launch_cfg(const TcGemmArgs& a, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+// Shared by both launchers: the epilogue's destination description.
+void fill_epilogue(const TcGemmArgs& a, Epilogue& ep) {
+  ep.M = a.M;
+  ep.N = a.N;
+  ep.K = a.K;
+  ep.C = a.C;
+  ep.c_plane = a.c_plane_elems;
+  ep.m_dst = a.m_dst;
+  ep.n_dst = a.n_dst;
+  ep.alpha = a.alpha;
+  int e2 = 0;
+  const double fr = std::frexp(a.alpha, &e2);  // alpha = fr * 2^e2, fr in [0.5, 1)
+  ep.alpha_pow2 = (fr == 0.5) ? 1 : 0;
+  ep.alpha_exp = e2 - 1;
+  ep.accumulate = a.accumulate;
+  ep.c_final = a.c_final ? 1 : 0;
+  int64_t hi = 0;  // largest column offset: 32-bit column offsets allowed below 2^31
+  for (int i = 0; i < a.n_dst.n; ++i) hi += (a.n_dst.dim[i] - 1) * a.n_dst.stride[i];
+  ep.off32 = hi < (int64_t(1) << 31) ? 1 : 0;
+}
+
+// Fixed-point split modes: S slice planes per operand, K split in whole
+// blocks of kOzBlockK.
+template <int S, int BN>
+cudaError_t launch_oz(const TcGemmArgs& a, cudaStream_t stream) {
+  using C = OzCfg<S, BN>;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(oz_gemm_kernel<S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::kSmem));
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  TMaps tm;
+  const char* A = static_cast<const char*>(a.A);
+  const char* B = static_cast<const char*>(a.B);
+  for (int pl = 0; pl < kMaxPlanes; ++pl) {
+    const int q = pl < S ? pl : 0;
+    if (!encode_operand(&tm.a[pl], A + q * a.a_plane_bytes, PREC_BF16, a.M, a.K, a.lda, kBM, C::kSlab))
+      return cudaErrorInvalidValue;
+    if (!encode_operand(&tm.b[pl], B + q * a.b_plane_bytes, PREC_BF16, a.N, a.K, a.ldb, BN, C::kSlab))
+      return cudaErrorInvalidValue;
+  }
+  Epilogue ep;
+  fill_epilogue(a, ep);
+  const int64_t num_k = (a.K + C::kBK - 1) / C::kBK;
+  const int64_t nblk = (a.K + kOzBlockK - 1) / kOzBlockK;
+  const int split = a.split > 1 && a.partial ? a.split : 1;
+  const int64_t per = (nblk + split - 1) / split;  // blocks per split
+  ep.split = split;
+  ep.kc = int(per * C::kBlockStages);
+  ep.partial = a.partial;
+  ep.p_plane = a.partial_plane;
+  if (split > 1 && ((split - 1) * per >= nblk || a.partial_plane < int64_t(split) * a.N * a.M))
+    return cudaErrorInvalidValue;  // an empty split, or lo partials overlapping hi
+  if (num_k <= 0) return cudaErrorInvalidValue;
+  const int64_t tiles = ((a.M + kBM - 1) / kBM) * ((a.N + BN - 1) / BN) * split;
+  static int resident = 0;
+  static std::once_flag occ_once;
+  std::call_once(occ_once, [] {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, oz_gemm_kernel<S, BN>, kOzThreads, C::kSmem);
+    resident = std::max(1, sms) * std::max(1, per_sm);
+  });
+  const unsigned grid = unsigned(std::min<int64_t>(tiles, resident));
+  count_launch();
+  oz_gemm_kernel<S, BN><<<grid, kOzThreads, C::kSmem, stream>>>(tm, ep);
+  if (split > 1) {
+    const unsigned gx = unsigned((a.M + 255) / 256);
+    const unsigned gy = unsigned(std::min<int64_t>(a.N, std::max<int64_t>(1, 4 * 152 / int64_t(gx))));
+    count_launch();
+    oz_splitk_reduce_kernel<<<dim3(gx, gy), 256, 0, stream>>>(ep);
+  }
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_oz_prec(const TcGemmArgs& a, cudaStream_t stream) {
+  const int bn = a.bn > 0 ? a.bn : (a.N > 64 ? 128 : (a.N > 16 ? 64 : 16));
+  switch (bn) {
+    case 128: return launch_oz<S, 128>(a, stream);
+    case 64: return launch_oz<S, 64>(a, stream);
+    case 16: return launch_oz<S, 16>(a, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int PREC>
 cudaError_t launch_prec(const TcGemmArgs& a, cudaStream_t stream) {
   switch (a.bn) {  // a width chosen by the planner (heuristic or autotuned)
@@ -697,6 +790,8 @@ cudaError_t launch_gemm_tc(const TcGemmArgs& a, cudaStream_t stream) {
     case PREC_BF16: return launch_prec<PREC_BF16>(a, stream);
     case PREC_BF16X3: return launch_prec<PREC_BF16X3>(a, stream);
     case PREC_BF16X6: return launch_prec<PREC_BF16X6>(a, stream);
+    case PREC_OZ3: return launch_oz_prec<3>(a, stream);
+    case PREC_OZ4: return launch_oz_prec<4>(a, stream);
     default: return cudaErrorNotSupported;
   }
 }

@@ -9,12 +9,14 @@
 namespace mera {
 
 // C[m_dst(m) + n_dst(n)] (+)= alpha * sum_k A[m, k] * B[n, k]
-// A: M x K operand matrix with row pitch lda elements (one or two planes),
-// B: N x K with pitch ldb.  Operands are TF32 (stored as FP32), BF16, or a
-// BF16 hi/lo pair (BF16X3: the lo plane follows the hi plane at
-// *_plane_bytes).  FP32 accumulation in tensor memory.  The destination is
-// either the caller's FP64 output (c_final) or the next operand buffer in
-// the same precision (c_plane_elems apart for the lo plane).
+// A: M x K operand matrix with row pitch lda elements (one or more planes),
+// B: N x K with pitch ldb.  Operands are TF32 (stored as FP32), BF16, or
+// BF16 planes of a split (BF16X3 hi/lo, BF16X6 hi/mid/lo, or the S slices of
+// the fixed-point split modes OZ3/OZ4), plane p at p * *_plane_bytes.  FP32
+// accumulation in tensor memory.  The destination is either the caller's
+// FP64 output (c_final) or the next operand buffer in the same precision
+// (c_plane_elems apart for the lower planes); in the fixed-point split modes
+// it is the raw hi + lo binary32 pair of the next operand, split afterwards.
 struct TcGemmArgs {
   int prec = 0;
   const void* A = nullptr;
@@ -30,7 +32,8 @@ struct TcGemmArgs {
   int accumulate = 0;
   int split = 1;             // K split (from tc_split_k); > 1 needs `partial`
   int bn = 0;                // tile width 16/64/128/256; 0: chosen from N
-  float* partial = nullptr;  // FP32 scratch [split][N][M]
+  float* partial = nullptr;  // FP32 scratch [split][N][M] (a second, lo plane in the fixed-point split modes)
+  int64_t partial_plane = 0; // fixed-point split modes: floats from the hi to the lo plane of `partial`
 };
 
 cudaError_t launch_gemm_tc(const TcGemmArgs& args, cudaStream_t stream);

@@ -117,19 +117,37 @@ def _emulate(plan, inputs, out_size, arena=None, reuse=False, keep=False):
                 assert b["bytes"] >= b["rows"] * b["ld"] * 4
             else:
                 assert b["ld"] * eb % 16 == 0  # TMA: row pitch multiple of 16 bytes
+            if b.get("raw"):  # hi and lo binary32 planes
+                assert b["bytes"] >= 2 * b["rows"] * b["ld"] * 4
         # stale data from an earlier diagram must never be read, except the
         # copies kept for the whole call (the leading persistent bytes)
         arena[plan["persistent_bytes"] // eb:] = np.nan
         for st in dg["steps"]:
             if st["kind"] == "permute" and st["skip"]:
-                b = bufs[st["dst_buf"]]
+                b = bufs[st["op_buf"]]
                 assert b["resident"] and b["offset"] + b["bytes"] <= plan["persistent_bytes"]
                 continue  # the same copy was made by an earlier step
-            if reuse and st["kind"] == "permute" and bufs[st["dst_buf"]]["resident"] == 1:
+            if st["kind"] == "split" and st["skip"]:
+                assert bufs[st["dst_buf"]]["resident"]
+                continue  # the split of that copy was made with it
+            if reuse and st["kind"] == "permute" and bufs[st["op_buf"]]["resident"] == 1:
                 continue  # u/w copy kept from the previous run
+            if reuse and st["kind"] == "split" and bufs[st["dst_buf"]]["resident"] == 1:
+                continue  # its split too
             if reuse and st["kind"] == "gemm" and st["stat"]:
-                assert bufs[st["c_buf"]]["resident"] == 1
+                assert bufs[st["c_buf"]]["resident"] == 1 or bufs[st["c_buf"]]["raw"]
                 continue  # u/w-only product kept from the previous run
+            if st["kind"] == "split":
+                # fixed-point split modes: raw hi + lo planes -> slices (same values here);
+                # every entry of the K columns of every row must have been written
+                r, d = bufs[st["raw_buf"]], bufs[st["dst_buf"]]
+                assert r["raw"] and not d["raw"] and st["K"] <= st["ld"] == d["ld"] == r["ld"]
+                assert st["rows"] == d["rows"] == r["rows"]
+                idx = np.arange(st["rows"])[:, None] * st["ld"] + np.arange(st["K"])[None, :]
+                vals = arena[r["offset"] // eb + idx]
+                assert not np.isnan(vals).any()
+                arena[d["offset"] // eb + idx] = vals
+                continue
             if st["kind"] == "permute":
                 src = inputs[st["slot"]].reshape(-1)
                 b = bufs[st["dst_buf"]]
@@ -174,8 +192,8 @@ _SMALL = [(1, 1), (2, 1), (2, 2), (3, 3), (2, 3), (4, 3), (3, 5)]
 
 
 @pytest.mark.parametrize("prec,chi_b,chi_t",
-                         [(p, b, t) for p in (m.PREC_F64, m.PREC_BF16X3, m.PREC_BF16X6) for b, t in _SMALL]
-                         + [(m.PREC_BF16X3, 4, 16)])  # first-layer shape, with K-split steps
+                         [(p, b, t) for p in (m.PREC_F64, m.PREC_BF16X3, m.PREC_BF16X6, m.PREC_OZ3) for b, t in _SMALL]
+                         + [(m.PREC_BF16X3, 4, 16), (m.PREC_OZ4, 4, 16)])  # first-layer shape, with K-split steps
 def test_programs_reproduce_oracle(prec, chi_b, chi_t):
     rng = np.random.default_rng(20)
     u, w = I.random_u(rng, chi_b), I.random_w(rng, chi_b, chi_t)
@@ -205,7 +223,7 @@ def forced_slicing():
 
 
 @pytest.mark.parametrize("prec,chi_b,chi_t", [(m.PREC_F64, 3, 3), (m.PREC_BF16X3, 2, 3), (m.PREC_F64, 4, 3),
-                                              (m.PREC_BF16X6, 3, 5)])
+                                              (m.PREC_BF16X6, 3, 5), (m.PREC_OZ3, 3, 4)])
 def test_sliced_programs_reproduce_oracle(forced_slicing, prec, chi_b, chi_t):
     _check_sliced(prec, chi_b, chi_t)
 
@@ -261,11 +279,12 @@ def test_slicing_shrinks_the_chi40_workspace():
     assert whole > 300 * 2**30
 
 
-def test_split_k_partials_do_not_overlap_live_buffers():
+@pytest.mark.parametrize("prec", [m.PREC_BF16X3, m.PREC_OZ3])
+def test_split_k_partials_do_not_overlap_live_buffers(prec):
     """Steps with few output tiles and long K get a K split; its FP32 partial
     buffer must not overlap the step's operands (the arena check above runs
     the same programs)."""
-    plan = m.mera_plan_json(m.OP_ENV_W, 4, 16, m.PREC_BF16X3)
+    plan = m.mera_plan_json(m.OP_ENV_W, 4, 16, prec)
     splits = [st for dg in plan["diagrams"] for st in dg["steps"] if st["kind"] == "gemm" and st["split"] > 1]
     assert splits, "the K = 65536 step of the 4 -> 16 env_w program should be split"
     for dg in plan["diagrams"]:
@@ -325,7 +344,7 @@ def test_identical_input_copies_are_made_once(op, chi):
         assert len(rho_copies) == 1
 
 
-@pytest.mark.parametrize("prec,chi", [(m.PREC_F64, 3), (m.PREC_BF16X3, 4)])
+@pytest.mark.parametrize("prec,chi", [(m.PREC_F64, 3), (m.PREC_BF16X3, 4), (m.PREC_OZ3, 4)])
 def test_rerun_with_kept_uw_products(prec, chi):
     """The power iteration runs the descending program again with new rho and
     the same u, w, skipping the u/w copies and the u/w-only products it kept:

@@ -107,12 +107,44 @@ def test_polar_update_f64(mm, nn):
 
 
 def test_polar_reports_nonconvergence_for_rank_deficient_input():
+    """The polar update is asynchronous: non-convergence within max_iter
+    steps is reported through the device status word, not a return code."""
     mm, nn = 16, 4
     env = np.zeros((mm, nn))
     env[0, 0] = 1.0  # rank 1: no unique polar factor
     out = torch.empty(mm * nn, dtype=torch.float64, device="cuda")
-    with pytest.raises(m.MeraNotConverged):
-        m.mera_polar_update(_cuda(env).reshape(-1), mm, nn, out, max_iter=30)
+    m.mera_device_status(clear=True)
+    m.mera_polar_update(_cuda(env).reshape(-1), mm, nn, out, max_iter=30)
+    torch.cuda.synchronize()
+    assert m.mera_device_status(clear=True) == 1 << 4  # MERA_ENOTCONV
+    # a converging update leaves the word clear
+    rng = np.random.default_rng(3)
+    m.mera_polar_update(_cuda(rng.standard_normal((mm, nn))).reshape(-1), mm, nn, out)
+    assert m.mera_device_status(clear=True) == 0
+
+
+def test_sweep_returns_before_its_stream_completes():
+    """Every compute call is asynchronous on its stream, the polar updates
+    of the direct sweep included: at chi = 16 a sweep runs ~60 ms on the GPU,
+    and the call returns while its stream is still busy."""
+    chi = 16
+    layers = I.init_mera(0, chi)
+    h1, shift = O.ising_h1(1.0)
+    st = m.MeraState([_cuda(u).reshape(-1).clone() for u, _ in layers], [_cuda(w).clone() for _, w in layers],
+                     _cuda(O.identity_density(chi)).reshape(-1).clone())
+    e = torch.empty(1, dtype=torch.float64, device="cuda")
+    h1d = _cuda(h1).reshape(-1)
+    stream = torch.cuda.Stream()
+    ws = m.workspace(m.mera_sweep_workspace_size(st.chi_b, st.chi_t, m.PREC_BF16X3))
+    m.mera_sweep(st, h1d, shift, 20, e, prec=m.PREC_BF16X3, ws=ws, stream=stream)  # plans, recordings
+    torch.cuda.synchronize()
+    busy = []
+    for _ in range(3):
+        m.mera_sweep(st, h1d, shift, 20, e, prec=m.PREC_BF16X3, ws=ws, stream=stream)
+        busy.append(not stream.query())
+        stream.synchronize()
+    assert all(busy)
+    assert m.mera_device_status(clear=True) == 0
 
 
 def test_argument_errors_do_not_launch():

@@ -200,6 +200,28 @@ def test_chi16_bf16x3_sampled_rows_and_properties():
     assert float(err) < MAP_TOL[prec]
 
 
+@pytest.mark.parametrize("prec,tol", [(m.PREC_F64, 1e-10), (m.PREC_BF16X3, None), (m.PREC_OZ4, 1e-8)])
+def test_descend_chi16_sampled_rows(prec, tol):
+    """The descending map at the benchmarked size (chi = 16; the rho* power
+    iteration applies it 20 times per sweep) against the oracle's rows with
+    the ket legs held fixed (oracle.descend_rows), entry by entry."""
+    chi = 16
+    tol = MAP_TOL[prec] if tol is None else tol
+    rng = np.random.default_rng(91)
+    u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
+    rho = I.random_density(rng, chi)
+    d = lambda x: _cuda(x).reshape(-1)  # noqa: E731
+    out = torch.empty(chi ** 6, dtype=torch.float64, device="cuda")
+    m.mera_descend(d(rho), d(u), d(w), chi, chi, out, prec=prec)
+    got = out.cpu().numpy().reshape((chi,) * 6)
+    rows = [(0, 0, 0), (7, 2, 13), (15, 15, 15), (9, 9, 4)]
+    want = O.descend_rows(rho, u, w, rows)
+    scale = np.abs(want).max()
+    errs = [float(np.abs(got[i, j, k] - want[n]).max() / scale) for n, (i, j, k) in enumerate(rows)]
+    print(f"prec={prec} chi=16 descend rows: max rel err {max(errs):.3e}")
+    assert max(errs) <= tol
+
+
 def _dot(a, b, chunk=1 << 30):
     """Dot product of long vectors (the BLAS dot takes at most 2^31 - 1)."""
     return sum(float(torch.dot(a[i:i + chunk], b[i:i + chunk])) for i in range(0, a.numel(), chunk))

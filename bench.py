@@ -608,6 +608,30 @@ def run_native(args):
                             f"descended, energy per spin, every map in the named mode",
                     "seconds": {args.prec: t1 - t0, "oz4": t2 - t1}}
 
+    # ---- the fixed-point split mode OZ4 at the headline chi ------------------
+    # (its sweep energies track FP64 to ~1e-9 per site; here its throughput
+    # and tensor-pipe rate at this size, against the FP64 sweep's estimate)
+    oz4 = None
+    if not args.no_accuracy and rank == 0 and prec != m.PREC_OZ4 and chi >= 24:
+        r = Run(m.PREC_OZ4, chi)
+        r.sweep()  # plans, recordings of the polar loops
+        m.mera_profile_enable(True)
+        ms, clk_oz = timed(r.sweep, 1, sample_clocks=True)
+        d4 = m.mera_profile_read(m.PROF_GEMM_DOMINANT)
+        c4 = m.mera_profile_read(m.PROF_PERMUTE)
+        m.mera_profile_enable(False)
+        tf4 = d4[2] / (d4[1] / 1e3) / 1e12 if d4[1] > 0 else None
+        pk4, pk4_src = _peak_tflops("oz4", sustained=True)
+        oz4 = {"sweeps_per_s": 1e3 / ms, "ms_per_step": ms, "steps": 1, "tflops": sweep_flops / ms / 1e9,
+               "energy_per_spin_after_2_sweeps": r.e.item(),
+               "dominant_tflops": tf4, "frac_of_mode_peak": (tf4 / pk4) if tf4 else None,
+               "peak": pk4, "peak_source": f"{pk4_src} bf16 / 10 products, of measured",
+               "copy_cast_split_ms": c4[1], "clocks": clk_oz,
+               "note": "one direct sweep after one warm sweep from the seeded start, per-kernel events"}
+        r.wsb = None
+        del r
+        torch.cuda.empty_cache()
+
     # ---- chi = 16: the plain FP64 GPU sweep and every mode's energy gap -------
     chi16 = None
     if args.fp64_steps > 0 and rank == 0:
@@ -652,6 +676,8 @@ def run_native(args):
                                            for k, v in outs.items() if k != "f64"},
                  "throughput": rates,
                  "fp64_sweeps_per_s_at_headline_chi_estimate": rates["f64"]["tflops"] * 1e12 / sweep_flops,
+                 "fp64_estimate_note": "the chi = 16 FP64 sweep's flop rate (the FP64 pipe limit) over the "
+                                       "headline chi's sweep flops",
                  "note": "one sweep from the seeded QR start in every mode; FP64 timed directly (its polar "
                          "updates and maps dominate), the others as replayed sweep graphs"}
 
@@ -674,6 +700,7 @@ def run_native(args):
         else "mera_sweep recorded once as a CUDA graph, replayed each step",
         "energy_per_spin": energy,
         "accuracy": accuracy,
+        "oz4": oz4,
         "chi16": chi16,
         "roofline": {"bound": "tensor" if args.prec != "f64" else "fp64", "achieved": dom_tflops, "peak": peak,
                      "unit": "TFLOP/s", "frac": (dom_tflops / peak) if dom_tflops else None,

@@ -89,6 +89,7 @@ typedef int mera_status;
 #define MERA_OP_ENV_W 3
 #define MERA_OP_ENERGY 4
 #define MERA_OP_FIXED_POINT 5
+#define MERA_OP_ENERGY_ADJOINT 6
 
 /* Largest bond dimension accepted by any entry point. */
 #define MERA_MAX_CHI 64
@@ -391,6 +392,25 @@ mera_status mera_profile_read(int kind, long long* launches, double* ms, double*
  */
 mera_status mera_op_transpose(const double* x, int d, double* out, void* stream);
 
+/*
+ * Adjoint of the energy term E = tr(A(h) rho) (Sec. II B; the gradients that
+ * Fig. A1's caption obtains by automatic differentiation), scaled by the
+ * upstream gradient *g_dev (a device double):
+ *   dh   = g D(rho^T)                          [chi_b^6]
+ *   drho = g A(h^T)                            [chi_t^6]
+ *   du   = g (Gamma_u(h, rho) + Gamma_u(h^T, rho^T))   [chi_b^4]
+ *   dw   = g (Gamma_w(h, rho) + Gamma_w(h^T, rho^T))   [chi_b^2 chi_t]
+ * with ^T the ket/bra transpose (A and D are adjoint; exchanging the ket and
+ * bra sides of the network transposes h and rho, so the ket-side holes are
+ * the environments of the transposed operators).  For symmetric h and rho,
+ * du = 2 g Gamma_u and dw = 2 g Gamma_w.  Any of dh, drho, du, dw may be
+ * NULL (not computed).  Nothing is kept between calls: every intermediate is
+ * recomputed.  Scratch: mera_workspace_size(MERA_OP_ENERGY_ADJOINT, ...).
+ */
+mera_status mera_energy_adjoint(const double* h, const double* rho, const double* u, const double* w, int chi_b,
+                                int chi_t, const double* g_dev, double* dh, double* drho, double* du, double* dw,
+                                int prec, void* ws, size_t ws_bytes, void* stream);
+
 /* Bytes of the device array that backs mera_ascend_noalloc (32 MiB). */
 #define MERA_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 
@@ -405,14 +425,16 @@ mera_status mera_op_transpose(const double* x, int d, double* out, void* stream)
  *
  * The scratch lives in a file-scope __device__ array of
  * MERA_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds
- * until the process exits (enough for chi_b = chi_t <= 8 in every mode, and
- * for the 4 -> 16 first layer).  Sizes whose mera_workspace_size(
+ * until the process exits (enough for chi_b = chi_t <= 8 in every mode but
+ * the fixed-point split ones, which need up to 37 MiB there, and for the
+ * 4 -> 16 first layer in every mode).  Sizes whose mera_workspace_size(
  * MERA_OP_ASCEND, ...) exceeds it are rejected with MERA_EINVAL and a
  * message.  No cudaMalloc, cudaFree or allocating library call is made.
  *
- * The first call on each device looks up the array's device address on the
- * current device (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the one array: every byte a call reads
+ * The first call on each device (and again after a device reset, which
+ * makes a new context) looks up the array's device address on the current
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array: every byte a call reads
  * is first written by that same call, so nothing has to start at zero, but
  * two calls that overlap on the GPU (different streams, or different host
  * threads) race on it and give undefined results.

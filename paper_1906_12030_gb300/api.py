@@ -21,7 +21,7 @@ __all__ = [
     "mera_energy", "mera_ising_h1", "mera_sweep", "mera_sweep_workspace_size", "mera_plan_json", "mera_flops",
     "workspace", "MeraState", "mera_launch_count", "mera_profile_enable", "mera_profile_read",
     "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE", "mera_device_status", "mera_gemm_test",
-    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_sweep_batch", "mera_set_slice_bytes",
+    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_energy_adjoint", "mera_sweep_batch", "mera_set_slice_bytes",
     "MeraGraph", "mera_sweep_graph", "mera_stiefel_step",
     "mera_stiefel_workspace_size", "mera_sweep_riemannian", "mera_autotune", "mera_autotune_reset",
     "mera_batch_lanes", "batch_resources", "mera_set_tile_width", "mera_tile_widths",
@@ -30,7 +30,7 @@ __all__ = [
 PREC_F64, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_BF16X6, PREC_OZ3, PREC_OZ4 = 0, 1, 2, 3, 4, 5, 6
 PRECS = {"f64": PREC_F64, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x3": PREC_BF16X3, "bf16x6": PREC_BF16X6,
          "oz3": PREC_OZ3, "oz4": PREC_OZ4}
-OP_ASCEND, OP_DESCEND, OP_ENV_U, OP_ENV_W, OP_ENERGY, OP_FIXED_POINT = 0, 1, 2, 3, 4, 5
+OP_ASCEND, OP_DESCEND, OP_ENV_U, OP_ENV_W, OP_ENERGY, OP_FIXED_POINT, OP_ENERGY_ADJOINT = 0, 1, 2, 3, 4, 5, 6
 MAX_LAYERS = 8
 PROF_GEMM, PROF_GEMM_DOMINANT, PROF_PERMUTE = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
@@ -103,6 +103,7 @@ def library():
             "mera_gemm_test": ([i, vp, vp, i, i, i, vp, vp, sz, vp], i),
             "mera_ascend_noalloc": ([vp, vp, vp, i, i, vp, i, vp], i),
             "mera_op_transpose": ([vp, i, vp, vp], i),
+            "mera_energy_adjoint": ([vp, vp, vp, vp, i, i, vp, vp, vp, vp, vp, i, vp, sz, vp], i),
             "mera_set_slice_bytes": ([sz], i),
             "mera_sweep_graph_create": ([ctypes.POINTER(_State), vp, d, i, i, vp, sz, vp, vp, ctypes.POINTER(vp)], i),
             "mera_graph_launch": ([vp, vp], i),
@@ -487,6 +488,21 @@ def mera_op_transpose(x, d, out, stream=None):
     """out[I, J] = x[J, I] for a 3-site operator of local dimension d."""
     _check(library().mera_op_transpose(_f64(x, d ** 6, "x"), d, _f64(out, d ** 6, "out"), _stream(stream)))
     return out
+
+
+def mera_energy_adjoint(h, rho, u, w, chi_b, chi_t, g, dh=None, drho=None, du=None, dw=None, prec=PREC_F64,
+                        ws=None, stream=None):
+    """Gradients of tr(A(h) rho) times the upstream gradient g (a one-element
+    device tensor): any of dh [chi_b^6], drho [chi_t^6], du [chi_b^4],
+    dw [chi_b^2 chi_t] that is given is written."""
+    ws = _auto_ws(ws, OP_ENERGY_ADJOINT, chi_b, chi_t, prec, h.device)
+    p, n = _ws(ws)
+    opt = lambda t, k, name: None if t is None else _f64(t, k, name)  # noqa: E731
+    _check(library().mera_energy_adjoint(
+        _f64(h, chi_b ** 6, "h"), _f64(rho, chi_t ** 6, "rho"), _f64(u, chi_b ** 4, "u"),
+        _f64(w, chi_b ** 2 * chi_t, "w"), chi_b, chi_t, _f64(g, 1, "g"), opt(dh, chi_b ** 6, "dh"),
+        opt(drho, chi_t ** 6, "drho"), opt(du, chi_b ** 4, "du"), opt(dw, chi_b ** 2 * chi_t, "dw"), prec, p, n,
+        _stream(stream)))
 
 
 def mera_sweep_batch(states, h1s, shifts, n_pow, e_out, prec=PREC_F64, wss=None, streams=None, n_threads=8):

@@ -293,6 +293,18 @@ static mera_status ws_size_impl(int op, int chi_b, int chi_t, int prec, size_t* 
       *bytes = op_bytes(*p) + align_up(ipow(chi_t, 6) * sizeof(double)) + kReduceBytes;
       return MERA_OK;
     }
+    case MERA_OP_ENERGY_ADJOINT: {
+      // transposes of h and rho, an environment half, then the largest map
+      size_t maps = 0;
+      for (int op2 : {OP_ASCEND, OP_DESCEND, OP_ENV_U, OP_ENV_W}) {
+        const OpProgram* p = get_program(op2, chi_b, chi_t, prec);
+        if (!p) return fail(MERA_EINVAL, "no contraction program");
+        maps = std::max(maps, op_bytes(*p));
+      }
+      *bytes = align_up(ipow(chi_b, 6) * sizeof(double)) + align_up(ipow(chi_t, 6) * sizeof(double)) +
+               align_up(std::max(ipow(chi_b, 4), ipow(chi_b, 2) * chi_t) * sizeof(double)) + maps;
+      return MERA_OK;
+    }
     case MERA_OP_FIXED_POINT: {
       if (chi_b != chi_t) return fail(MERA_EINVAL, "fixed point needs chi_b == chi_t");
       const OpProgram* p = get_program(OP_DESCEND, chi_b, chi_t, prec);
@@ -522,7 +534,11 @@ std::mutex mu;
 std::map<Key, Entry> cache;
 unsigned long long tick = 0;
 
-void* current_context() {
+}  // namespace polar_detail
+
+// The driver context current on the calling thread (cuCtxGetCurrent through
+// the runtime's driver entry point; nullptr if unavailable).
+void* current_cu_context() {
   using GetCtx = int (*)(void**);
   static GetCtx fn = nullptr;
   static std::once_flag once;
@@ -538,7 +554,6 @@ void* current_context() {
   return ctx;
 }
 
-}  // namespace polar_detail
 }  // namespace mera
 
 extern "C" mera_status mera_polar_update(const double* env, int m, int n, double* out, int max_iter, double tol,
@@ -557,7 +572,7 @@ extern "C" mera_status mera_polar_update(const double* env, int m, int n, double
   if (cap != cudaStreamCaptureStatusNone) return polar_record(env, m, n, out, max_iter, tol, ws, ws_bytes, s);
   // Direct call: launch the cached instantiation of the recording (made on
   // the first call with these arguments).
-  const Key key{current_context(), env, out, ws, ws_bytes, m, n, max_iter, tol};
+  const Key key{current_cu_context(), env, out, ws, ws_bytes, m, n, max_iter, tol};
   std::lock_guard<std::mutex> lk(mu);
   auto it = cache.find(key);
   if (it == cache.end()) {
@@ -991,6 +1006,49 @@ extern "C" mera_status mera_op_transpose(const double* x, int d, double* out, vo
   st.row_src.n = 1; st.row_src.dim[0] = n; st.row_src.stride[0] = 1;
   st.col_src.n = 1; st.col_src.dim[0] = n; st.col_src.stride[0] = n;
   return cuda_status(launch_permute(st, x, out, 0, PREC_F64, static_cast<cudaStream_t>(stream)), "transpose");
+}
+
+extern "C" mera_status mera_energy_adjoint(const double* h, const double* rho, const double* u, const double* w,
+                                           int chi_b, int chi_t, const double* g_dev, double* dh, double* drho,
+                                           double* du, double* dw, int prec, void* ws, size_t ws_bytes,
+                                           void* stream) {
+  size_t need = 0;
+  mera_status st = ws_size_impl(MERA_OP_ENERGY_ADJOINT, chi_b, chi_t, prec, &need);
+  if (st != MERA_OK) return st;
+  if (!h || !rho || !u || !w || !g_dev) return fail(MERA_EINVAL, "null input pointer");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(MERA_EINVAL, "workspace not 256-byte aligned");
+  if (!ws || ws_bytes < need) return fail(MERA_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Arena ar{static_cast<char*>(ws), ws_bytes};
+  const int64_t nb = ipow(chi_b, 6), nt = ipow(chi_t, 6);
+  double* ht = reinterpret_cast<double*>(ar.take(nb * sizeof(double)));
+  double* rt = reinterpret_cast<double*>(ar.take(nt * sizeof(double)));
+  double* half = reinterpret_cast<double*>(ar.take(std::max(ipow(chi_b, 4), ipow(chi_b, 2) * chi_t) * sizeof(double)));
+  void* mws = ar.ptr();
+  const size_t mb = ar.left();
+  if ((st = mera_op_transpose(h, chi_b, ht, stream)) != MERA_OK) return st;
+  if ((st = mera_op_transpose(rho, chi_t, rt, stream)) != MERA_OK) return st;
+  cudaError_t e = cudaSuccess;
+  if (dh) {  // dE/dh = D(rho^T)
+    if ((st = mera_descend(rt, u, w, chi_b, chi_t, dh, prec, mws, mb, stream)) != MERA_OK) return st;
+    if ((e = launch_scaled_sum(dh, nullptr, g_dev, dh, nb, s)) != cudaSuccess) return cuda_status(e, "scale");
+  }
+  if (drho) {  // dE/drho = A(h^T)
+    if ((st = mera_ascend(ht, u, w, chi_b, chi_t, drho, prec, mws, mb, stream)) != MERA_OK) return st;
+    if ((e = launch_scaled_sum(drho, nullptr, g_dev, drho, nt, s)) != cudaSuccess) return cuda_status(e, "scale");
+  }
+  if (du) {  // dE/du = Gamma_u(h, rho) + Gamma_u(h^T, rho^T)
+    if ((st = mera_env_u(h, rho, u, w, chi_b, chi_t, du, prec, mws, mb, stream)) != MERA_OK) return st;
+    if ((st = mera_env_u(ht, rt, u, w, chi_b, chi_t, half, prec, mws, mb, stream)) != MERA_OK) return st;
+    if ((e = launch_scaled_sum(du, half, g_dev, du, ipow(chi_b, 4), s)) != cudaSuccess) return cuda_status(e, "sum");
+  }
+  if (dw) {  // dE/dw = Gamma_w(h, rho) + Gamma_w(h^T, rho^T)
+    if ((st = mera_env_w(h, rho, u, w, chi_b, chi_t, dw, prec, mws, mb, stream)) != MERA_OK) return st;
+    if ((st = mera_env_w(ht, rt, u, w, chi_b, chi_t, half, prec, mws, mb, stream)) != MERA_OK) return st;
+    if ((e = launch_scaled_sum(dw, half, g_dev, dw, ipow(chi_b, 2) * chi_t, s)) != cudaSuccess)
+      return cuda_status(e, "sum");
+  }
+  return MERA_OK;
 }
 
 extern "C" mera_status mera_sweep_batch(mera_state* states, int n, const double* const* h1, const double* shift,

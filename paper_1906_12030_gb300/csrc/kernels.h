@@ -14,6 +14,10 @@ namespace mera {
 extern std::atomic<long long> g_launch_count;
 inline void count_launch(long long n = 1) { g_launch_count.fetch_add(n, std::memory_order_relaxed); }
 
+// The driver context current on the calling thread (an opaque key for
+// per-context caches: a device reset makes a new context).
+void* current_cu_context();
+
 // Input tensor -> operand layout, cast to the operand precision (in the
 // fixed-point split modes: to the raw hi + lo binary32 planes).
 cudaError_t launch_permute(const PermuteStep& p, const double* src, void* dst, int64_t plane_elems,
@@ -74,6 +78,9 @@ cudaError_t launch_ns_output(const double* x0, const double* x1, const int* stat
 cudaError_t launch_stiefel_sym(const double* A, double* S, int64_t n, cudaStream_t stream);
 cudaError_t launch_stiefel_combine(const double* X, const double* G, const double* T, double* Yneg, int64_t count,
                                    double eta, cudaStream_t stream);
+// out = g * (a + b) elementwise (b may be null), g a device scalar.
+cudaError_t launch_scaled_sum(const double* a, const double* b, const double* g, double* out, int64_t n,
+                              cudaStream_t stream);
 // Sets the conditional handle of a recorded while loop to (state[0] == 0 and
 // state[1] < max_iter).
 cudaError_t launch_ns_continue(const int* state, cudaGraphConditionalHandle h, int max_iter, cudaStream_t stream);

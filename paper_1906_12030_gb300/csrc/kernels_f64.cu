@@ -700,4 +700,24 @@ cudaError_t launch_ns_continue(const int* state, cudaGraphConditionalHandle h, i
 }
 
 
+// out = g * (a + b) elementwise (b may be null), g a device scalar: the
+// energy adjoint's sum of the two environment halves times the upstream
+// gradient.
+__global__ void __launch_bounds__(256) scaled_sum_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                                         const double* __restrict__ g, double* __restrict__ out,
+                                                         int64_t n) {
+  const double gv = *g;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = gv * (b ? a[i] + b[i] : a[i]);
+}
+
+cudaError_t launch_scaled_sum(const double* a, const double* b, const double* g, double* out, int64_t n,
+                              cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned grid = unsigned(std::min<int64_t>((n + 255) / 256, 152 * 8));
+  count_launch();
+  scaled_sum_kernel<<<grid, 256, 0, stream>>>(a, b, g, out, n);
+  return cudaGetLastError();
+}
+
 }  // namespace mera

@@ -16,6 +16,7 @@
 
 namespace mera {
 mera_status set_last_error(mera_status st, const char* msg);
+void* current_cu_context();
 }
 
 namespace {
@@ -23,19 +24,23 @@ namespace {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MERA_NOALLOC_SCRATCH_BYTES];
 
 std::mutex g_noalloc_mu;
-std::map<int, void*> g_noalloc_addr;  // device ordinal -> device address of the array
+// (device ordinal, driver context) -> device address of the array.  The
+// context is part of the key: after a device reset the device's new primary
+// context loads the module again, possibly at another address.
+std::map<std::pair<int, void*>, void*> g_noalloc_addr;
 
 // Device address of the array on the current device, looked up once per
-// device.  In host code `g_noalloc_scratch` only names a host-side shadow,
-// so it must never be handed to a kernel directly.
+// device and context.  In host code `g_noalloc_scratch` only names a
+// host-side shadow, so it must never be handed to a kernel directly.
 mera_status scratch_address(void** out, const char** why) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     *why = "cudaGetDevice failed";
     return MERA_ECUDA;
   }
+  const std::pair<int, void*> key{dev, mera::current_cu_context()};
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  auto it = g_noalloc_addr.find(dev);
+  auto it = g_noalloc_addr.find(key);
   if (it != g_noalloc_addr.end()) {
     *out = it->second;
     return MERA_OK;
@@ -45,7 +50,9 @@ mera_status scratch_address(void** out, const char** why) {
     *why = "cudaGetSymbolAddress of the static scratch array failed";
     return MERA_ECUDA;
   }
-  g_noalloc_addr[dev] = p;
+  // the lookup made the device's context current if none was: file the
+  // address under that context
+  g_noalloc_addr[{dev, mera::current_cu_context()}] = p;
   *out = p;
   return MERA_OK;
 }

@@ -65,10 +65,11 @@ def test_operator_transpose():
     assert np.array_equal(out.cpu().numpy().reshape(want.shape), want)
 
 
-# Map tolerances of the tensor-core modes (relative to the largest FP64 entry),
-# the same bounds the map parity tests derive from the operand and accumulator
-# precision of each mode.
-_MODE_TOL = {m.PREC_TF32: 5e-3, m.PREC_BF16X3: 5e-4}
+# Tolerances of the tensor-core modes (relative to the largest FP64 entry):
+# the map parity tests' bounds for each mode (TF32 5e-3, BF16X3 8e-5), and
+# twice that for BF16X3, whose u and w gradients sum two environments; the
+# fixed-point split mode OZ4 at its map tolerance (1.2e-7), doubled likewise.
+_MODE_TOL = {m.PREC_TF32: 5e-3, m.PREC_BF16X3: 1.6e-4, m.PREC_OZ4: 2.4e-7}
 
 
 def _grads(h, rho, u, w, chi_b, chi_t, prec):
@@ -104,8 +105,8 @@ def test_adjoint_against_central_differences_chi12():
 
 @pytest.mark.parametrize("chi", [12, 16])
 def test_mixed_precision_adjoint_against_fp64(chi):
-    """The adjoint with TF32 and split-BF16 contractions (FP32 accumulation)
-    matches the FP64 adjoint entry by entry within each mode's map tolerance."""
+    """The adjoint with TF32, split-BF16 and fixed-point split contractions
+    matches the FP64 adjoint entry by entry within each mode's tolerance."""
     rng = np.random.default_rng(81 + chi)
     u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
     h = I.random_operator(rng, chi, symmetric=False)
@@ -113,8 +114,11 @@ def test_mixed_precision_adjoint_against_fp64(chi):
     e64, g64 = _grads(h, rho, u, w, chi, chi, m.PREC_F64)
     for prec, tol in _MODE_TOL.items():
         e, gs = _grads(h, rho, u, w, chi, chi, prec)
-        for name, g, want in zip(("h", "rho", "u", "w"), gs, g64):
-            assert np.abs(g - want).max() <= tol * np.abs(want).max(), (prec, name)
+        errs = {name: float(np.abs(g - want).max() / np.abs(want).max())
+                for name, g, want in zip(("h", "rho", "u", "w"), gs, g64)}
+        print(f"prec={prec} chi={chi} adjoint errors {errs}")
+        for name, err in errs.items():
+            assert err <= tol, (prec, name, err)
 
 
 @pytest.mark.parametrize("prec", [m.PREC_TF32, m.PREC_BF16X3])

@@ -124,3 +124,31 @@ def test_scratch_shared_across_streams_is_rejected():
         m.mera_sweep_batch([b[0] for b in batch], [b[1] for b in batch], [b[2] for b in batch], 20, e,
                            wss=[ws, ws], streams=[torch.cuda.Stream(), torch.cuda.Stream()])
     assert m.mera_launch_count() == n0
+
+
+@pytest.mark.parametrize("prec,tol", [(m.PREC_F64, 1e-10), (m.PREC_OZ4, 1e-8)])
+def test_batched_meras_match_the_oracle(prec, tol):
+    """Every member of a batch (different h and chi) against the FP64
+    oracle's sweeps of the same MERA: energies per spin after each of three
+    sweeps, and the tensors after the last."""
+    specs = [(30, 3, 0.93), (31, 4, 1.0), (32, 4, 1.07), (33, 5, 0.97)]
+    batch = [_mera(*sp) for sp in specs]
+    eb = torch.empty(len(specs), dtype=torch.float64, device="cuda")
+    oracle = []
+    for seed, chi, hz in specs:
+        h1, shift = O.ising_h1(hz)
+        oracle.append(([(u.copy(), w.copy()) for u, w in I.init_mera(seed, chi)], h1, shift,
+                       O.identity_density(chi)))
+    for _ in range(3):
+        m.mera_sweep_batch([b[0] for b in batch], [b[1] for b in batch], [b[2] for b in batch], 20, eb,
+                           prec=prec, n_threads=4)
+        got = eb.cpu().numpy()
+        for i, (layers, h1, shift, rho) in enumerate(oracle):
+            layers, rho, e = O.sweep(layers, h1, shift, rho, 20)
+            oracle[i] = (layers, h1, shift, rho)
+            assert abs(got[i] - e) <= tol * abs(e), (i, got[i], e)
+    for (st, _, _), (layers, _, _, _) in zip(batch, oracle):
+        for (ou, ow), u, w in zip(layers, st.us, st.ws):
+            assert np.abs(u.cpu().numpy().reshape(ou.shape) - ou).max() < 1e3 * tol
+            assert np.abs(w.cpu().numpy().reshape(ow.shape) - ow).max() < 1e3 * tol
+    assert m.mera_device_status(clear=True) == 0

@@ -289,3 +289,39 @@ def test_scaling_dimensions_of_the_optimised_chi4_mera():
     assert got[0] == pytest.approx(d_id, abs=1e-9)
     assert abs(got[1] - d_sigma) < 0.003 and abs(got[2] - d_eps) < 0.002
     assert np.all(np.abs(got[3:5] - cft["sigma_descendant"]["value"]) < 0.005) and got[5] > 1.5
+
+
+def test_fp64_sweeps_replayed_by_the_oracle_from_checkpoints():
+    """The plain FP64 GPU run compared with the oracle from its own
+    checkpoints: the GPU state after sweeps 1, 2 and 40 of a chi = 8 run is
+    copied out, the oracle runs the next sweep from it, and the GPU's next
+    sweep matches (energy to 1e-10 relative, u, w and rho* to 1e-9)."""
+    chi, last = 8, 41
+    checkpoints = {1, 2, 40}
+    layers = I.init_mera(0, chi)
+    h1, shift = O.ising_h1(1.0)
+    st = m.MeraState([_cuda(u).reshape(-1).clone() for u, _ in layers], [_cuda(w).clone() for _, w in layers],
+                     _cuda(O.identity_density(chi)).reshape(-1).clone())
+    e = torch.empty(1, dtype=torch.float64, device="cuda")
+    h1d = _cuda(h1).reshape(-1)
+    ws = m.workspace(m.mera_sweep_workspace_size(st.chi_b, st.chi_t, m.PREC_F64))
+    shapes = [(u.shape, w.shape) for u, w in layers]
+    snap = None
+    n_checked = 0
+    for k in range(1, last + 1):
+        m.mera_sweep(st, h1d, shift, 20, e, ws=ws)
+        if snap is not None:  # k = checkpoint + 1: the oracle's sweep from the snapshot
+            ol, orho, oe = O.sweep(snap[0], h1, shift, snap[1], 20)
+            assert e.item() == pytest.approx(oe, rel=1e-10, abs=0)
+            for (ou, ow), u, w in zip(ol, st.us, st.ws):
+                assert np.abs(u.cpu().numpy().reshape(ou.shape) - ou).max() < 1e-9
+                assert np.abs(w.cpu().numpy().reshape(ow.shape) - ow).max() < 1e-9
+            assert np.abs(st.rho_star.cpu().numpy().reshape(orho.shape) - orho).max() < 1e-9
+            n_checked += 1
+            snap = None
+        if k in checkpoints:
+            snap = ([(u.cpu().numpy().reshape(su), w.cpu().numpy().reshape(sw))
+                     for (su, sw), u, w in zip(shapes, st.us, st.ws)],
+                    st.rho_star.cpu().numpy().reshape((chi,) * 6))
+    assert n_checked == len(checkpoints)
+    assert m.mera_device_status(clear=True) == 0

@@ -12,9 +12,13 @@ Map tolerances (relative to the largest oracle entry): a diagram is ~10
 chained contractions, each rounding its result to the operand precision
 once (~10 u in a random walk, x2 for the even + odd / 4-6 hole sums) and
 accumulating up to K = chi_t^3 products in FP32.  TF32: 10 u = 5e-3.
-BF16: 10 u = 4e-2 (3e-2 kept, 3x the measured 9e-3).  BF16X3: 10 u =
-2.3e-4 plus the FP32 accumulation bound K 2^-24 = 2.4e-4 at K = 4096,
-i.e. 5e-4.
+BF16: 10 u = 4e-2 (3e-2 kept, 3x the measured 9e-3).  BF16X3: the random
+walk of ~10 roundings to the 16-bit pair, sqrt(10) * 2^-17 = 2.4e-5, plus
+the FP32 accumulation over K <= 4096; measured at most 2.9e-5 over these
+shapes and the chi = 16 rows, so 8e-5 (about 3x; the bound 10 u + K 2^-24
+= 5e-4 would let a tenfold regression pass).  The error grows with K: at
+chi = 32 (K up to 32768) a descending map is ~2.4e-4 from the fixed-point
+split mode OZ4 (bench.py's accuracy block).
 BF16X6: the binary64 -> FP32 conversion (2^-24), the three-part split of
 the FP32 value (2^-25) and the dropped products (mid*lo, lo*mid, lo*lo,
 below 2^-23 |a b| together) fit in 2u with u = 2^-22; its maps are
@@ -34,7 +38,7 @@ pytestmark = pytest.mark.gpu
 
 U_OPERAND = {m.PREC_TF32: 2.0 ** -11 + 2.0 ** -24, m.PREC_BF16: 2.0 ** -8, m.PREC_BF16X3: 1.5 * 2.0 ** -16,
              m.PREC_BF16X6: 2.0 ** -22}
-MAP_TOL = {m.PREC_TF32: 5e-3, m.PREC_BF16: 3e-2, m.PREC_BF16X3: 5e-4, m.PREC_BF16X6: 4e-5}
+MAP_TOL = {m.PREC_TF32: 5e-3, m.PREC_BF16: 3e-2, m.PREC_BF16X3: 8e-5, m.PREC_BF16X6: 4e-5}
 TC_PRECS = [m.PREC_TF32, m.PREC_BF16, m.PREC_BF16X3, m.PREC_BF16X6]
 
 

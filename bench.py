@@ -901,13 +901,16 @@ def run_batch(args):
 
 
 def run_precision(args):
-    """Mixed precision against FP64 on the same MERA (same seed, same sweep count):
-    - ref:    S sweeps with FP64 contractions;
+    """Mixed precision against a reference mode (--ref-prec: FP64, or the
+    fixed-point split mode OZ4 where FP64 sweeps take hours) on the same MERA
+    (same seed, same sweep count):
+    - ref:    S sweeps in the reference mode;
     - mixed:  S sweeps in the mixed mode;
-    - polish: S - P mixed sweeps, then P FP64 sweeps.
-    Each final state is evaluated in FP64 (rho* by 60 power steps from its warm
-    start, descent to the bottom layer, energy per spin); the mixed state is
-    also evaluated in the mixed mode.  All contractions run in the library."""
+    - polish: S - P mixed sweeps, then P sweeps in the reference mode.
+    Each final state is evaluated in the reference mode (rho* by 60 power
+    steps from its warm start, descent to the bottom layer, energy per spin);
+    the mixed state is also evaluated in the mixed mode.  All contractions
+    run in the library."""
     import numpy as np
     import torch
 
@@ -917,6 +920,7 @@ def run_precision(args):
 
     dev = torch.device("cuda", 0)
     chi, prec = args.chi, m.PRECS[args.prec]
+    ref = m.PRECS[args.ref_prec]
     h1_host, shift = m.mera_ising_h1(HZ)
     h1 = torch.from_numpy(h1_host.reshape(-1)).to(dev)
     S, P = args.sweeps, min(args.polish, args.sweeps)
@@ -970,19 +974,20 @@ def run_precision(args):
         m.mera_energy(h1, rho, us[0], ws_[0], cb, ct, e, prec=p)
         return 0.5 * (float(e.item()) + shift)
 
-    out = {"case": "precision", "chi": chi, "prec": args.prec, "sweeps": S, "polish_fp64_sweeps": P, "z2": args.z2,
-           "exact_infinite_chain": -4.0 / np.pi}
+    out = {"case": "precision", "chi": chi, "prec": args.prec, "sweeps": S, "polish_ref_sweeps": P, "z2": args.z2,
+           "exact_infinite_chain": -4.0 / np.pi,
+           "ref_mode": args.ref_prec}
     st, us, ws_, rho = fresh()
     hist_m, t_m = run(st, [prec] * S)
     out["mixed"] = {"sweep_energy_last": hist_m[-1], "sweep_energy_change_last10": hist_m[-1] - hist_m[-11]
                     if S > 10 else None, "seconds": t_m,
-                    "energy_fp64_eval": evaluate(us, ws_, rho, m.PREC_F64),
+                    "energy_ref_eval": evaluate(us, ws_, rho, ref),
                     "energy_mixed_eval": evaluate(us, ws_, rho, prec)}
-    out["mixed"]["dE_eval_mixed_vs_fp64"] = abs(out["mixed"]["energy_mixed_eval"] - out["mixed"]["energy_fp64_eval"])
+    out["mixed"]["dE_eval_mixed_vs_ref"] = abs(out["mixed"]["energy_mixed_eval"] - out["mixed"]["energy_ref_eval"])
     if args.scaling_k > 0:
-        d64 = scaling.scaling_dimensions(us[-1], ws_[-1], chi, k=args.scaling_k, prec=m.PREC_F64, tol=1e-10)
+        d64 = scaling.scaling_dimensions(us[-1], ws_[-1], chi, k=args.scaling_k, prec=ref, tol=1e-10)
         dmx = scaling.scaling_dimensions(us[-1], ws_[-1], chi, k=args.scaling_k, prec=prec, tol=1e-10)
-        out["mixed"]["scaling_dims_fp64"] = [float(x) for x in d64]
+        out["mixed"]["scaling_dims_ref"] = [float(x) for x in d64]
         out["mixed"]["scaling_dims_max_abs_err"] = float(np.max(np.abs(d64 - dmx)))
     if args.riemannian_eta > 0:
         st, us, ws_, rho = fresh()
@@ -1000,7 +1005,7 @@ def run_precision(args):
         out["riemannian"] = {"eta": args.riemannian_eta, "sweep_energy_last": hr[-1],
                              "sweep_energy_at_quarter": hr[max(0, S // 4 - 1)],
                              "seconds": time.perf_counter() - t0,
-                             "energy_fp64_eval": evaluate(us, ws_, rho, m.PREC_F64)}
+                             "energy_ref_eval": evaluate(us, ws_, rho, ref)}
         out["mixed"]["sweep_energy_at_quarter"] = hist_m[max(0, S // 4 - 1)]
     if args.grow_from > 0:
         from paper_1906_12030_gb300 import grow
@@ -1016,21 +1021,21 @@ def run_precision(args):
         out["grown"] = {"from_chi": args.grow_from, "sweeps_before": args.grow_sweeps,
                         "energy_before_growth": h0[-1], "sweep_energy_last": hist_g[-1],
                         "seconds": t0 + t_g,
-                        "energy_fp64_eval": evaluate(stg.us, stg.ws, stg.rho_star, m.PREC_F64)}
+                        "energy_ref_eval": evaluate(stg.us, stg.ws, stg.rho_star, ref)}
     if P > 0:
         st, us, ws_, rho = fresh()
-        hist_p, t_p = run(st, [prec] * (S - P) + [m.PREC_F64] * P)
+        hist_p, t_p = run(st, [prec] * (S - P) + [ref] * P)
         out["polish"] = {"sweep_energy_last": hist_p[-1], "seconds": t_p,
-                         "energy_fp64_eval": evaluate(us, ws_, rho, m.PREC_F64)}
+                         "energy_ref_eval": evaluate(us, ws_, rho, ref)}
     if args.fp64_steps > 0:
         st, us, ws_, rho = fresh()
-        hist_r, t_r = run(st, [m.PREC_F64] * S)
-        e_ref = evaluate(us, ws_, rho, m.PREC_F64)
-        out["ref_fp64"] = {"sweep_energy_last": hist_r[-1], "sweep_energy_change_last10": hist_r[-1] - hist_r[-11]
-                           if S > 10 else None, "seconds": t_r, "energy_fp64_eval": e_ref}
-        out["mixed"]["dE_vs_fp64_ground_state"] = abs(out["mixed"]["energy_fp64_eval"] - e_ref)
+        hist_r, t_r = run(st, [ref] * S)
+        e_ref = evaluate(us, ws_, rho, ref)
+        out["ref_run"] = {"sweep_energy_last": hist_r[-1], "sweep_energy_change_last10": hist_r[-1] - hist_r[-11]
+                           if S > 10 else None, "seconds": t_r, "energy_ref_eval": e_ref}
+        out["mixed"]["dE_vs_ref_run"] = abs(out["mixed"]["energy_ref_eval"] - e_ref)
         if P > 0:
-            out["polish"]["dE_vs_fp64_ground_state"] = abs(out["polish"]["energy_fp64_eval"] - e_ref)
+            out["polish"]["dE_vs_ref_run"] = abs(out["polish"]["energy_ref_eval"] - e_ref)
     print(json.dumps(out), flush=True)
 
 

@@ -150,6 +150,9 @@ def test_adjoint_at_chi24_recomputes_and_satisfies_euler_identities(prec):
     ev = e.item()
     assert ev > 0
     degree = {"h": 1, "rho": 1, "u": 4, "w": 6}
+    # at K = chi^3 = 13824 the FP32 accumulation dominates: the derived map
+    # bound 10 u + K 2^-24 (TF32 5e-3; BF16X3 1.05e-3, measured 5e-4)
+    tol = {m.PREC_TF32: 5e-3, m.PREC_BF16X3: 10 * 1.5 * 2.0 ** -16 + chi ** 3 * 2.0 ** -24}[prec]
     for (name, k), x, t in zip(degree.items(), (h, rho, u, w), ts):
         lhs = float(torch.sum(t.grad * t.detach()))
-        assert lhs == pytest.approx(k * ev, rel=_MODE_TOL[prec]), (name, lhs, k * ev)
+        assert lhs == pytest.approx(k * ev, rel=tol), (name, lhs, k * ev)

@@ -126,11 +126,11 @@ def test_scratch_shared_across_streams_is_rejected():
     assert m.mera_launch_count() == n0
 
 
-@pytest.mark.parametrize("prec,tol", [(m.PREC_F64, 1e-10), (m.PREC_OZ4, 1e-8)])
-def test_batched_meras_match_the_oracle(prec, tol):
+@pytest.mark.parametrize("prec,tol,tol_x", [(m.PREC_F64, 1e-11, 1e-8), (m.PREC_OZ4, 1e-8, 1e-5)])
+def test_batched_meras_match_the_oracle(prec, tol, tol_x):
     """Every member of a batch (different h and chi) against the FP64
     oracle's sweeps of the same MERA: energies per spin after each of three
-    sweeps, and the tensors after the last."""
+    sweeps (to tol), and the tensors after the last (to tol_x)."""
     specs = [(30, 3, 0.93), (31, 4, 1.0), (32, 4, 1.07), (33, 5, 0.97)]
     batch = [_mera(*sp) for sp in specs]
     eb = torch.empty(len(specs), dtype=torch.float64, device="cuda")
@@ -146,9 +146,9 @@ def test_batched_meras_match_the_oracle(prec, tol):
         for i, (layers, h1, shift, rho) in enumerate(oracle):
             layers, rho, e = O.sweep(layers, h1, shift, rho, 20)
             oracle[i] = (layers, h1, shift, rho)
-            assert abs(got[i] - e) <= tol * abs(e), (i, got[i], e)
+            assert abs(got[i] - e) <= tol, (i, got[i], e)
     for (st, _, _), (layers, _, _, _) in zip(batch, oracle):
         for (ou, ow), u, w in zip(layers, st.us, st.ws):
-            assert np.abs(u.cpu().numpy().reshape(ou.shape) - ou).max() < 1e3 * tol
-            assert np.abs(w.cpu().numpy().reshape(ow.shape) - ow).max() < 1e3 * tol
+            assert np.abs(u.cpu().numpy().reshape(ou.shape) - ou).max() < tol_x
+            assert np.abs(w.cpu().numpy().reshape(ow.shape) - ow).max() < tol_x
     assert m.mera_device_status(clear=True) == 0

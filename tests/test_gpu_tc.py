@@ -42,6 +42,15 @@ MAP_TOL = {m.PREC_TF32: 5e-3, m.PREC_BF16: 3e-2, m.PREC_BF16X3: 8e-5, m.PREC_BF1
 TC_PRECS = [m.PREC_TF32, m.PREC_BF16, m.PREC_BF16X3, m.PREC_BF16X6]
 
 
+def bf16x3_tol(chi):
+    """BF16X3 map tolerance at bond dimension chi: MAP_TOL (measured) while
+    the contractions have K = chi^3 <= 4096, the derived bound 10 u + K 2^-24
+    beyond, where the FP32 accumulation over K grows (measured 2.0e-4 at
+    chi = 32 and 4.1e-4 at chi = 40 against bounds of 2.2e-3 and 4.0e-3)."""
+    k = chi ** 3
+    return MAP_TOL[m.PREC_BF16X3] if k <= 4096 else 10 * U_OPERAND[m.PREC_BF16X3] + k * 2.0 ** -24
+
+
 def _cuda(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
@@ -240,6 +249,7 @@ def test_full_size_properties(chi):
     - tr D(rho) = tr rho;
     - duality <A(h), rho> = <h, D(rho)> (D is the adjoint of A)."""
     prec = m.PREC_BF16X3
+    tol = bf16x3_tol(chi)
     rng = np.random.default_rng(chi)
     u, w = I.random_u(rng, chi), I.random_w(rng, chi, chi)
     ud, wd = _cuda(u).reshape(-1), _cuda(w).reshape(-1)
@@ -253,7 +263,7 @@ def test_full_size_properties(chi):
     err = float((out.reshape(n3, n3).diagonal() - 1.0).abs().max())
     out.reshape(n3, n3).diagonal().zero_()
     err = max(err, float(out.abs().max()))
-    assert err < MAP_TOL[prec], err
+    assert err < tol, err
     # duality and trace with random (non-symmetric) h and rho
     x.normal_(generator=g)  # h
     rho = torch.empty_like(x).normal_(generator=g)
@@ -263,10 +273,10 @@ def test_full_size_properties(chi):
     m.mera_descend(rho, ud, wd, chi, chi, out, prec=prec, ws=ws)
     rhs = _dot(x, out)
     # both sides carry the maps' error relative to |h| |rho|
-    assert abs(lhs - rhs) <= MAP_TOL[prec] * hn * rn, (lhs, rhs)
+    assert abs(lhs - rhs) <= tol * hn * rn, (lhs, rhs)
     tr_in = float(rho.reshape(n3, n3).diagonal().sum())
     tr_out = float(out.reshape(n3, n3).diagonal().sum())
-    assert abs(tr_out - tr_in) <= MAP_TOL[prec] * float(rho.reshape(n3, n3).diagonal().abs().sum()) + 1e-9
+    assert abs(tr_out - tr_in) <= tol * float(rho.reshape(n3, n3).diagonal().abs().sum()) + 1e-9
     torch.cuda.synchronize()
 
 

@@ -104,8 +104,11 @@ def _args():
                     help="--case precision: scaling dimensions (FP64 and mixed Arnoldi) of the final state")
     ap.add_argument("--ref-prec", default="f64", choices=["f64", "oz4", "oz3"],
                     help="--case precision: the mode of the reference run")
+    ap.add_argument("--spectrum-chis", default="8,16",
+                    help="--case spectrum: bond dimensions of the growth ladder (parity-symmetric MERA)")
+    ap.add_argument("--spectrum-sweeps", default="6000,10000", help="--case spectrum: sweeps at each of them")
     ap.add_argument("--case", default="sweep",
-                    choices=["sweep", "ascend", "descend", "env_u", "env_w", "batch", "precision"])
+                    choices=["sweep", "ascend", "descend", "env_u", "env_w", "batch", "precision", "spectrum"])
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)  # internal: oracle timing child
     return ap.parse_args()
 
@@ -165,7 +168,8 @@ def _peak_tflops(prec: str, sustained: bool = True):
 # DRAM bytes per launch of the chi^9-class GEMMs, from the ncu capture named
 # here (profiles/).  Reported only for the workload it was taken on; it must
 # be retaken (or set to None) whenever the kernel changes.
-ROOFLINE_TRAFFIC = {("bf16x3", 16): (1.128e9, "profiles/tc_gemm_bf16x3_chi16_ascend.md (autotuned widths)")}
+ROOFLINE_TRAFFIC = {("bf16x3", 32): (17.46e9, "profiles/tc_gemm_bf16x3_chi32_descend_dram.md (48 chi^9-class "
+                                              "launches of the descending map, the sweep's most frequent, per launch)")}
 
 
 def _layer_dims(chi: int):
@@ -558,27 +562,29 @@ def run_native(args):
                                             "stream give the roofline and the stage split"}
 
     # ---- end to end through the C ABI with host buffers ---------------------
+    # (mera_sweep_host: the state and h1 copied in from pinned host memory,
+    # the sweep -- a replay of the recorded graph --, the energy copied out)
     e2e = None
     if not args.no_e2e:
-        devs = run.us + run.ws + [run.rho, h1]
-        host = [t.detach().cpu().pin_memory() for t in devs]
+        host_us = [t.detach().reshape(-1).cpu().pin_memory() for t in run.us]
+        host_ws = [t.detach().reshape(-1).cpu().pin_memory() for t in run.ws]
+        host_rho = run.rho.detach().cpu().pin_memory()
+        host_h1 = h1.detach().cpu().pin_memory()
         e_host = torch.empty(1, dtype=torch.float64).pin_memory()
-        h2d = sum(t.numel() * t.element_size() for t in host)
+        h2d = sum(t.numel() * t.element_size() for t in host_us + host_ws + [host_rho, host_h1])
         n_e2e = max(1, min(args.steps, 3))
 
         def e2e_step():
-            for hsrc, ddst in zip(host, devs):
-                ddst.copy_(hsrc, non_blocking=True)
-            run.step()
-            e_host.copy_(run.e, non_blocking=True)
+            m.mera_sweep_host(run.st, host_us, host_ws, host_rho, host_h1, h1, shift, N_POW, run.e, e_host,
+                              prec=prec, ws=run.wsb, graph=run.graph, stream=stream)
 
         e2e_ms, _ = timed(e2e_step, n_e2e)
         e2e_ms = _max_over_ranks(e2e_ms, dev)
         e2e = {"value": _job_throughput(world, n_e2e, e2e_ms), "unit": "sweep/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 8, "steps": n_e2e,
-               "path": "graph replay" if run.graph is not None else "mera_sweep",
-               "note": "per step: the state (u, w of every layer, rho*, h1) copied in from pinned host memory, "
-                       "one sweep, the energy copied out"}
+               "path": "mera_sweep_host (graph replay)" if run.graph is not None else "mera_sweep_host",
+               "note": "per step, one C-ABI call: the state (u, w of every layer, rho*, h1) copied in from pinned "
+                       "host memory, one sweep, the energy copied out"}
     run.close()
     run.wsb = None  # the sweep scratch is not needed for the evaluations below
     torch.cuda.empty_cache()
@@ -1039,6 +1045,84 @@ def run_precision(args):
     print(json.dumps(out), flush=True)
 
 
+def run_spectrum(args):
+    """Scaling dimensions of the Ising CFT (Sec. III A, Fig. 7) from a
+    parity-symmetric MERA optimised up a ladder of bond dimensions: Z2 start
+    at the first, sweeps in the chosen mode (recorded sweep graphs replayed),
+    growth to the next with the parity kept (grow.grow_state(z2=True)), and
+    so on.  The final state's energy per spin (rho* by 60 power steps from
+    its warm start, descent, energy) and the 12 lowest scaling dimensions of
+    its scale-invariant ascending map are evaluated with the fixed-point split
+    mode OZ4."""
+    import numpy as np
+    import torch
+
+    import mera_inputs as I
+    import paper_1906_12030_gb300 as m
+    from paper_1906_12030_gb300 import grow, scaling
+
+    dev = torch.device("cuda", 0)
+    prec = m.PRECS[args.prec]
+    chis = [int(x) for x in args.spectrum_chis.split(",")]
+    counts = [int(x) for x in args.spectrum_sweeps.split(",")]
+    h1n, shift = m.mera_ising_h1(HZ)
+    h1 = torch.from_numpy(h1n.reshape(-1)).to(dev)
+    layers = I.init_mera(SEED, chis[0], z2=True)
+    st = m.MeraState([torch.from_numpy(u).to(dev).reshape(-1).contiguous() for u, _ in layers],
+                     [torch.from_numpy(w).to(dev).contiguous() for _, w in layers],
+                     (torch.eye(chis[0] ** 3, dtype=torch.float64, device=dev) / chis[0] ** 3).reshape(-1))
+    stages = []
+    for i, (chi, n) in enumerate(zip(chis, counts)):
+        if i > 0:
+            st = grow.grow_state(st, I.layer_dims(chi), seed=SEED + i, eps=1e-4, z2=True,
+                                 bottom_parity=I.parity_labels(4, physical=True))
+        stream = torch.cuda.Stream(dev)
+        e = torch.empty(1, dtype=torch.float64, device=dev)
+        wsb = m.workspace(m.mera_sweep_workspace_size(st.chi_b, st.chi_t, prec), dev)
+        g = m.mera_sweep_graph(st, h1, shift, N_POW, e, prec=prec, ws=wsb, stream=stream)
+        hist = torch.empty(max(1, n // 100), dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(n):
+                g.launch(stream)
+                if (k + 1) % 100 == 0:
+                    hist[(k + 1) // 100 - 1:(k + 1) // 100].copy_(e)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        g.close()
+        del wsb
+        torch.cuda.empty_cache()
+        h = hist.cpu().tolist()
+        stages.append({"chi": chi, "sweeps": n, "seconds": dt, "sweep_energy_last": h[-1],
+                       "energy_every_100": h[:: max(1, len(h) // 20)]})
+    status = m.mera_device_status(clear=True)
+    chi = chis[-1]
+    dims = I.layer_dims(chi)
+    oz4 = m.PREC_OZ4
+    rho = st.rho_star.clone()
+    ws_fp = m.workspace(m.mera_workspace_size(m.OP_FIXED_POINT, chi, chi, oz4), dev)
+    m.mera_fixed_point_rho(st.us[-1], st.ws[-1], chi, rho, 60, prec=oz4, ws=ws_fp)
+    for t in range(len(dims) - 2, 0, -1):
+        cb, ct = dims[t]
+        out = torch.empty(cb ** 6, dtype=torch.float64, device=dev)
+        m.mera_descend(rho, st.us[t], st.ws[t], cb, ct, out, prec=oz4)
+        rho = out
+    ee = torch.empty(1, dtype=torch.float64, device=dev)
+    m.mera_energy(h1, rho, st.us[0], st.ws[0], dims[0][0], dims[0][1], ee, prec=oz4)
+    energy = 0.5 * (float(ee.item()) + shift)
+    exact = -4.0 / np.pi
+    deltas = scaling.scaling_dimensions(st.us[-1], st.ws[-1], chi, k=12, prec=oz4, tol=1e-10)
+    cft = [0.0, 0.125, 1.0, 1.125, 1.125]
+    print(json.dumps({"case": "spectrum", "prec": args.prec, "stages": stages, "chi": chi,
+                      "energy_per_spin_oz4": energy, "exact_infinite_chain": exact,
+                      "relative_energy_error": (energy - exact) / abs(exact),
+                      "scaling_dims_oz4": [float(x) for x in deltas],
+                      "ising_cft_lowest": cft,
+                      "abs_dev_lowest5": [float(abs(a - b)) for a, b in zip(deltas[:5], cft)],
+                      "device_status": status}), flush=True)
+
+
 def main():
     args = _args()
     if args.cpu_sample:
@@ -1052,6 +1136,9 @@ def main():
         return
     if args.case == "precision":
         run_precision(args)
+        return
+    if args.case == "spectrum":
+        run_spectrum(args)
         return
     if args.case != "sweep":
         run_case(args)

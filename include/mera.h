@@ -358,6 +358,25 @@ mera_status mera_sweep_graph_create(mera_state* S, const double* h1, double shif
 mera_status mera_graph_launch(mera_graph graph, void* stream);
 mera_status mera_graph_destroy(mera_graph graph);
 
+/*
+ * One sweep of a MERA whose tensors come from HOST memory (Sec. II C; the
+ * host-buffer form of mera_sweep).  On `stream`: copies u_host[k]
+ * (chi_b[k]^4 doubles) and w_host[k] (chi_b[k]^2 chi_t[k]) of every layer
+ * into S's device tensors, rho_host (chi_t[last]^6) into S->rho_star and
+ * h1_host (chi_b[0]^6) into h1_dev, then runs the sweep -- a replay of
+ * `graph` when it is not NULL (a sweep recorded with mera_sweep_graph_create
+ * on these same device buffers), else mera_sweep(S, h1_dev, shift, n_pow,
+ * prec, ws, ws_bytes, e_dev) -- and copies the energy per spin *e_dev to
+ * *e_host.  The updated tensors stay on the device.  Asynchronous: the host
+ * buffers must stay valid until the stream has passed the copies, and they
+ * should be page-locked for the copies to overlap nothing else on the host;
+ * *e_host is valid once the stream is synchronised.
+ */
+mera_status mera_sweep_host(mera_state* S, const double* const* u_host, const double* const* w_host,
+                            const double* rho_host, const double* h1_host, double* h1_dev, double shift, int n_pow,
+                            int prec, void* ws, size_t ws_bytes, double* e_dev, double* e_host, mera_graph graph,
+                            void* stream);
+
 /* ------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper; used to measure the kernels).
  * ---------------------------------------------------------------------- */

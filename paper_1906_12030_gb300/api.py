@@ -21,7 +21,7 @@ __all__ = [
     "mera_energy", "mera_ising_h1", "mera_sweep", "mera_sweep_workspace_size", "mera_plan_json", "mera_flops",
     "workspace", "MeraState", "mera_launch_count", "mera_profile_enable", "mera_profile_read",
     "PROF_GEMM", "PROF_GEMM_DOMINANT", "PROF_PERMUTE", "mera_device_status", "mera_gemm_test",
-    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_energy_adjoint", "mera_sweep_batch", "mera_set_slice_bytes",
+    "mera_ascend_noalloc", "NOALLOC_SCRATCH_BYTES", "mera_op_transpose", "mera_energy_adjoint", "mera_sweep_host", "mera_sweep_batch", "mera_set_slice_bytes",
     "MeraGraph", "mera_sweep_graph", "mera_stiefel_step",
     "mera_stiefel_workspace_size", "mera_sweep_riemannian", "mera_autotune", "mera_autotune_reset",
     "mera_batch_lanes", "batch_resources", "mera_set_tile_width", "mera_tile_widths",
@@ -107,6 +107,8 @@ def library():
             "mera_set_slice_bytes": ([sz], i),
             "mera_sweep_graph_create": ([ctypes.POINTER(_State), vp, d, i, i, vp, sz, vp, vp, ctypes.POINTER(vp)], i),
             "mera_graph_launch": ([vp, vp], i),
+            "mera_sweep_host": ([ctypes.POINTER(_State), ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp, d, i, i,
+                                 vp, sz, vp, vp, vp, vp], i),
             "mera_graph_destroy": ([vp], i),
             "mera_stiefel_workspace_size": ([i, i, ctypes.POINTER(sz)], i),
             "mera_stiefel_step": ([vp, vp, i, i, d, vp, vp, sz, vp], i),
@@ -328,6 +330,34 @@ def mera_sweep(state: MeraState, h1, shift, n_pow, e_out, prec=PREC_F64, ws=None
     _check(library().mera_sweep(ctypes.byref(st), _f64(h1, state.chi_b[0] ** 6, "h1"), float(shift), n_pow, prec, p,
                                 n, _f64(e_out, 1, "e_out"), _stream(stream)))
     return e_out
+
+
+def mera_sweep_host(state: MeraState, us_host, ws_host, rho_host, h1_host, h1, shift, n_pow, e_dev, e_host,
+                    prec=PREC_F64, ws=None, graph=None, stream=None):
+    """One sweep with the inputs taken from host tensors (pinned CPU float64
+    tensors: u and w of every layer, rho*, h1) copied into `state` and `h1`
+    (device) on the stream, the energy copied back into e_host (a pinned
+    one-element CPU tensor).  graph: a MeraGraph recorded on these device
+    buffers, replayed instead of a direct sweep."""
+    if graph is None and ws is None:
+        ws = workspace(mera_sweep_workspace_size(state.chi_b, state.chi_t, prec), h1.device)
+    p, n = _ws(ws) if ws is not None else (None, 0)
+    st = state._c()
+
+    def host_ptr(t, numel, name):
+        if t.element_size() != 8 or t.is_cuda or not t.is_contiguous() or t.numel() != numel:
+            raise ValueError(f"{name}: a contiguous CPU float64 tensor of {numel} elements is needed")
+        return ctypes.c_void_p(t.data_ptr())
+
+    nl = len(state.us)
+    ups = (ctypes.c_void_p * nl)(*[host_ptr(t, state.chi_b[k] ** 4, f"u[{k}]") for k, t in enumerate(us_host)])
+    wps = (ctypes.c_void_p * nl)(*[host_ptr(t, state.chi_b[k] ** 2 * state.chi_t[k], f"w[{k}]")
+                                   for k, t in enumerate(ws_host)])
+    _check(library().mera_sweep_host(
+        ctypes.byref(st), ups, wps, host_ptr(rho_host, state.chi_t[-1] ** 6, "rho"),
+        host_ptr(h1_host, state.chi_b[0] ** 6, "h1"), _f64(h1, state.chi_b[0] ** 6, "h1_dev"), float(shift), n_pow,
+        prec, p, n, _f64(e_dev, 1, "e_dev"), host_ptr(e_host, 1, "e_host"),
+        graph._h if graph is not None else None, _stream(stream)))
 
 
 class MeraGraph:

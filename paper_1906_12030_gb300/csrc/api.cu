@@ -814,6 +814,8 @@ extern "C" mera_status mera_sweep_riemannian(mera_state* S, const double* h1, do
 // ---------------------------------------------------------------------------
 // A sweep recorded once as a CUDA graph and replayed.
 // ---------------------------------------------------------------------------
+struct mera_graph_s;
+extern "C" mera_status mera_graph_launch(mera_graph g, void* stream);
 struct mera_graph_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -858,6 +860,33 @@ extern "C" mera_status mera_graph_launch(mera_graph g, void* stream) {
   if (e != cudaSuccess) return cuda_status(e, "graph launch");
   count_launch(g->launches);
   return MERA_OK;
+}
+
+extern "C" mera_status mera_sweep_host(mera_state* S, const double* const* u_host, const double* const* w_host,
+                                       const double* rho_host, const double* h1_host, double* h1_dev, double shift,
+                                       int n_pow, int prec, void* ws, size_t ws_bytes, double* e_dev, double* e_host,
+                                       mera_graph graph, void* stream) {
+  if (!S || !u_host || !w_host || !rho_host || !h1_host || !h1_dev || !e_dev || !e_host)
+    return fail(MERA_EINVAL, "null argument to mera_sweep_host");
+  const int n = S->n_layers;
+  if (n < 1 || n > MERA_MAX_LAYERS) return fail(MERA_EINVAL, "bad n_layers %d", n);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto up = [&](double* dst, const double* src, int64_t count) {
+    return cudaMemcpyAsync(dst, src, size_t(count) * sizeof(double), cudaMemcpyHostToDevice, s);
+  };
+  cudaError_t e = cudaSuccess;
+  for (int t = 0; t < n && e == cudaSuccess; ++t) {
+    if (!S->u[t] || !S->w[t] || !u_host[t] || !w_host[t]) return fail(MERA_EINVAL, "null tensor in layer %d", t);
+    e = up(S->u[t], u_host[t], ipow(S->chi_b[t], 4));
+    if (e == cudaSuccess) e = up(S->w[t], w_host[t], ipow(S->chi_b[t], 2) * S->chi_t[t]);
+  }
+  if (e == cudaSuccess) e = up(S->rho_star, rho_host, ipow(S->chi_t[n - 1], 6));
+  if (e == cudaSuccess) e = up(h1_dev, h1_host, ipow(S->chi_b[0], 6));
+  if (e != cudaSuccess) return cuda_status(e, "host to device copies");
+  mera_status st = graph ? mera_graph_launch(graph, stream)
+                         : mera_sweep(S, h1_dev, shift, n_pow, prec, ws, ws_bytes, e_dev, stream);
+  if (st != MERA_OK) return st;
+  return cuda_status(cudaMemcpyAsync(e_host, e_dev, sizeof(double), cudaMemcpyDeviceToHost, s), "energy copy");
 }
 
 extern "C" mera_status mera_graph_destroy(mera_graph g) {

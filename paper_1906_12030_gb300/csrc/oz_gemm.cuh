@@ -139,8 +139,9 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       uint32_t it = 0;
       bool alive = true;
       for (int64_t t = blockIdx.x; t < tiles && alive; t += gridDim.x) {
-        const int64_t mn = t % tiles_mn;
-        const int m0 = int((mn / tiles_n) * kBM), n0 = int((mn % tiles_n) * BN);
+        int64_t row_t, col_t;
+        tile_of(t % tiles_mn, tiles_mn / tiles_n, tiles_n, ep.group_m, row_t, col_t);
+        const int m0 = int(row_t * kBM), n0 = int(col_t * BN);
         const int kb0 = int(t / tiles_mn) * ep.kc, kb1 = min(kb0 + ep.kc, num_k);
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const uint32_t s = it % C::kStages;
@@ -225,8 +226,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const bool raw_fast = !ep.c_final && ep.split <= 1 && ep.off32 && ep.alpha == 1.0;
     uint32_t bc = 0;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-      const int64_t mn = t % tiles_mn, ks = t / tiles_mn;
-      const int64_t m0 = (mn / tiles_n) * kBM, n0 = (mn % tiles_n) * BN;
+      const int64_t ks = t / tiles_mn;
+      int64_t row_t, col_t;
+      tile_of(t % tiles_mn, tiles_mn / tiles_n, tiles_n, ep.group_m, row_t, col_t);
+      const int64_t m0 = row_t * kBM, n0 = col_t * BN;
       const int kb0 = int(ks) * ep.kc, kb1 = min(kb0 + ep.kc, num_k);
       asm volatile("bar.sync 1, %0;" ::"n"(kOzEpiThreads) : "memory");
       if (et == 0) *abort_snapshot = *abort_flag;

@@ -186,7 +186,22 @@ struct Epilogue {
   int off32;        // every column offset n_dst(n) is below 2^31
   int alpha_exp;    // alpha == 2^alpha_exp exactly (alpha_pow2 set)
   int alpha_pow2;
+  int group_m;      // tile order: groups of this many row tiles, every column tile of a group in turn
 };
+
+// Output tile (row tile, column tile) of the mn-th tile in the kernels' walk
+// order.  Tiles are taken in groups of group_m row tiles; within a group the
+// column tile changes slowest, so one column tile of B meets group_m row
+// tiles of A while both are in L2, and the group's A rows (sized by the host
+// to a fraction of L2) stay resident across the group's column tiles.
+__device__ __forceinline__ void tile_of(int64_t mn, int64_t tiles_m, int64_t tiles_n, int group_m, int64_t& tm,
+                                        int64_t& tn) {
+  const int64_t per_group = int64_t(group_m) * tiles_n;
+  const int64_t g = mn / per_group, r = mn - g * per_group;
+  const int64_t rows = min(int64_t(group_m), tiles_m - g * group_m);  // row tiles in this group
+  tn = r / rows;
+  tm = g * group_m + (r - tn * rows);
+}
 
 // binary32 -> binary64 times 2^e by integer operations, exact for every
 // class of input (zero, subnormal, normal, infinity, NaN; e must keep a
@@ -331,8 +346,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t it = 0;
       bool alive = true;
       for (int64_t t = blockIdx.x; t < tiles && alive; t += gridDim.x) {
-        const int64_t mn = t % tiles_mn;
-        const int m0 = int((mn / tiles_n) * kBM), n0 = int((mn % tiles_n) * BN);
+        int64_t row_t, col_t;
+        tile_of(t % tiles_mn, tiles_mn / tiles_n, tiles_n, ep.group_m, row_t, col_t);
+        const int m0 = int(row_t * kBM), n0 = int(col_t * BN);
         const int kb0 = int(t / tiles_mn) * ep.kc, kb1 = min(kb0 + ep.kc, num_k);
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const uint32_t s = it % C::kStages;
@@ -411,8 +427,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool final_fast = ep.c_final && ep.split <= 1 && ep.off32 && ep.alpha_pow2;
     uint32_t tc = 0;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++tc) {
-      const int64_t mn = t % tiles_mn, ks = t / tiles_mn;
-      const int64_t m0 = (mn / tiles_n) * kBM, n0 = (mn % tiles_n) * BN;
+      const int64_t ks = t / tiles_mn;
+      int64_t row_t, col_t;
+      tile_of(t % tiles_mn, tiles_mn / tiles_n, tiles_n, ep.group_m, row_t, col_t);
+      const int64_t m0 = row_t * kBM, n0 = col_t * BN;
       const uint32_t b = tc & 1;
       // all epilogue threads are done with the previous tile's offsets;
       // decide together whether to go on
@@ -599,6 +617,15 @@ bool encode_operand(CUtensorMap* tm, const void* base, int prec, int64_t rows, i
   return r == CUDA_SUCCESS;
 }
 
+// Row tiles per group of the tile walk (tile_of): as many as keep the
+// group's A rows within 32 MB (a quarter of L2), at least one.
+int group_rows(const TcGemmArgs& a, int64_t a_row_bytes) {
+  const int64_t tile_bytes = int64_t(kBM) * a_row_bytes;
+  const int64_t tiles_m = (a.M + kBM - 1) / kBM;
+  const int64_t g = std::max<int64_t>(1, (int64_t(32) << 20) / std::max<int64_t>(1, tile_bytes));
+  return int(std::min<int64_t>(g, tiles_m));
+}
+
 template <int PREC, int BN>
 cudaError_t launch_cfg(const TcGemmArgs& a, cudaStream_t stream) {
   using C = Cfg<PREC, BN>;
@@ -649,6 +676,7 @@ cudaError_t launch_cfg(const TcGemmArgs& a, cudaStream_t stream) {
     for (int i = 0; i < a.n_dst.n; ++i) hi += (a.n_dst.dim[i] - 1) * a.n_dst.stride[i];
     ep.off32 = hi < (int64_t(1) << 31) ? 1 : 0;
   }
+  ep.group_m = group_rows(a, a.K * C::kElem * C::kPlanes);
   if (split > 1 && (int64_t(split - 1) * ep.kc >= num_k)) return cudaErrorInvalidValue;  // empty split
   const int64_t tiles = ((a.M + kBM - 1) / kBM) * ((a.N + BN - 1) / BN) * split;
   if (tiles <= 0) return cudaErrorInvalidValue;
@@ -694,6 +722,7 @@ void fill_epilogue(const TcGemmArgs& a, Epilogue& ep) {
   ep.off32 = hi < (int64_t(1) << 31) ? 1 : 0;
 }
 
+
 // Fixed-point split modes: S slice planes per operand, K split in whole
 // blocks of kOzBlockK.
 template <int S, int BN>
@@ -717,6 +746,7 @@ cudaError_t launch_oz(const TcGemmArgs& a, cudaStream_t stream) {
   }
   Epilogue ep;
   fill_epilogue(a, ep);
+  ep.group_m = group_rows(a, a.K * 2 * S);
   const int64_t num_k = (a.K + C::kBK - 1) / C::kBK;
   const int64_t nblk = (a.K + kOzBlockK - 1) / kOzBlockK;
   const int split = a.split > 1 && a.partial ? a.split : 1;

@@ -101,3 +101,47 @@ def test_grown_mera_contains_the_smaller_one():
     # variational: above the exact energy, and the warm start loses nothing
     # (one more sweep with more freedom lowers it further)
     assert -4.0 / np.pi - 1e-9 <= e_big <= e_small + 1e-4
+
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_sweep_from_host_buffers_equals_the_device_sweep(use_graph):
+    """mera_sweep_host (the state copied in from pinned host memory, the
+    sweep, the energy copied out) gives bit for bit the device sweep of the
+    same state."""
+    chi, prec = 4, m.PREC_BF16X3
+    layers = I.init_mera(3, chi)
+    h1n, shift = m.mera_ising_h1(1.0)
+
+    def state():
+        us = [torch.from_numpy(u).cuda().reshape(-1).contiguous() for u, _ in layers]
+        ws = [torch.from_numpy(w).cuda().contiguous() for _, w in layers]
+        rho = (torch.eye(chi ** 3, dtype=torch.float64, device="cuda") / chi ** 3).reshape(-1).contiguous()
+        return m.MeraState(us, ws, rho)
+
+    ref = state()
+    h1 = torch.from_numpy(h1n.reshape(-1)).cuda()
+    e_ref = torch.empty(1, dtype=torch.float64, device="cuda")
+    m.mera_sweep(ref, h1, shift, 20, e_ref, prec=prec)
+    # host copies of the initial state, then the same sweep through host buffers
+    hu = [torch.from_numpy(u.reshape(-1).copy()).pin_memory() for u, _ in layers]
+    hw = [torch.from_numpy(w.reshape(-1).copy()).pin_memory() for _, w in layers]
+    hrho = (torch.eye(chi ** 3, dtype=torch.float64) / chi ** 3).reshape(-1).contiguous().pin_memory()
+    hh1 = torch.from_numpy(h1n.reshape(-1).copy()).pin_memory()
+    dev = state()
+    for t in dev.us + dev.ws + [dev.rho_star]:
+        t.zero_()  # the copies must bring the whole state in
+    h1d = torch.zeros_like(h1)
+    e_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+    e_host = torch.zeros(1, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.Stream()
+    ws = m.workspace(m.mera_sweep_workspace_size(dev.chi_b, dev.chi_t, prec))
+    graph = m.mera_sweep_graph(dev, h1d, shift, 20, e_dev, prec=prec, ws=ws, stream=stream) if use_graph else None
+    m.mera_sweep_host(dev, hu, hw, hrho, hh1, h1d, shift, 20, e_dev, e_host, prec=prec, ws=ws, graph=graph,
+                      stream=stream)
+    stream.synchronize()
+    assert float(e_host[0]) == e_ref.item()
+    for a, b in zip(ref.us + ref.ws + [ref.rho_star], dev.us + dev.ws + [dev.rho_star]):
+        assert torch.equal(a, b)
+    if graph is not None:
+        graph.close()

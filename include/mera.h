@@ -267,10 +267,15 @@ mera_status mera_sweep_batch(mera_state* states, int n, const double* const* h1,
  * device access).  MERA i has n_layers layers with dimensions
  * chi_b[i * n_layers + k], chi_t[i * n_layers + k]; its scratch is
  * mera_sweep_workspace_size and its cost the contraction flops of one sweep
- * with n_pow power steps.  Longest-processing-time-first list scheduling:
- * MERAs are taken by decreasing scratch (then cost); each opens a new lane
- * while fewer than max_lanes exist and its scratch fits in what is left of
- * budget_bytes, otherwise it joins the lane with the least cost so far.
+ * with n_pow power steps.  MERAs whose sweep alone fills the GPU (at least
+ * 1e13 flops, e.g. chi >= 16 with tau* = 3) all go to lane 0, one after
+ * another: their GEMMs are persistent kernels over every SM, and two of them
+ * side by side only contend (measured: 0.94x of one at a time for a 32-MERA
+ * mix of chi 8..32 with one lane each).  The others get longest-processing-
+ * time-first list scheduling: taken by decreasing scratch (then cost), each
+ * opens a new lane while fewer than max_lanes exist and its scratch fits in
+ * what is left of budget_bytes, otherwise it joins the lane with the least
+ * cost so far.
  * Outputs: lane[i] in [0, *n_lanes) for every MERA, and lane_bytes[l] (room
  * for n entries) the scratch of lane l, which covers each of its members;
  * the lane_bytes sum to at most budget_bytes.  MERA_ENOMEM if the largest

@@ -1147,11 +1147,14 @@ static double sweep_flops(int n, const int* cb, const int* ct, int n_pow) {
   return tot;
 }
 
-// Lanes of a batch: longest-processing-time-first list scheduling under a cap
-// on the summed scratch.  MERAs are taken by decreasing scratch size (then
-// cost); each opens a lane while lanes and budget remain, else joins the
-// least-loaded lane, whose scratch (sized by its first, largest member)
-// already holds it.
+// Lanes of a batch.  A MERA whose sweep alone fills the GPU (at least
+// kFillFlops contraction flops: its GEMMs are persistent kernels over every
+// SM, and two of them side by side only contend for the SMs and L2) joins
+// one shared lane, so those run back to back.  The others get
+// longest-processing-time-first list scheduling under a cap on the summed
+// scratch: taken by decreasing scratch size (then cost), each opens a lane
+// while lanes and budget remain, else joins the least-loaded lane, whose
+// scratch (sized by its first, largest member) already holds it.
 extern "C" mera_status mera_batch_lanes(int n, int n_layers, const int* chi_b, const int* chi_t, int prec, int n_pow,
                                         size_t budget_bytes, int max_lanes, int* lane, int* n_lanes,
                                         size_t* lane_bytes) {
@@ -1181,8 +1184,27 @@ extern "C" mera_status mera_batch_lanes(int n, int n_layers, const int* chi_b, c
   std::vector<size_t> bytes;
   std::vector<double> load;
   size_t used = 0;
+  constexpr double kFillFlops = 1e13;  // a chi = 16 sweep (2.0e13) fills the GPU; chi = 12 (1.5e12) does not
+  size_t big_need = 0;
+  double big_load = 0.0;
+  for (int i = 0; i < n; ++i)
+    if (cost[size_t(i)] >= kFillFlops) {
+      big_need = std::max(big_need, need[size_t(i)]);
+      big_load += cost[size_t(i)];
+    }
+  if (big_need > 0) {  // the shared lane of the GPU-filling MERAs is lane 0
+    if (big_need > budget_bytes)
+      return fail(MERA_ENOMEM, "a MERA needs %zu bytes of scratch; the budget is %zu", big_need, budget_bytes);
+    bytes.push_back(big_need);
+    load.push_back(big_load);
+    used = big_need;
+  }
   for (int i : order) {
     const size_t b = need[size_t(i)];
+    if (cost[size_t(i)] >= kFillFlops) {
+      lane[i] = 0;
+      continue;
+    }
     if (int(bytes.size()) < max_lanes && b <= budget_bytes - used) {
       lane[i] = int(bytes.size());
       bytes.push_back(b);

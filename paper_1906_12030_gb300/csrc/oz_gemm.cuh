@@ -23,8 +23,10 @@
 // Tensor memory: (G0, G1) x 2 buffers of width BN (<= 128), so the MMAs of
 // block k+1 overlap the epilogue's reads of block k.  Warp roles as in
 // tc_gemm_kernel (warp 0 TMA, warp 1 MMA) with eight epilogue warps; stages
-// hold 64-byte slabs (32 BF16 along K) of every plane, so eight stages make
-// one block.
+// hold 64-byte slabs (32 BF16 along K) of every plane -- the A planes, then
+// the B planes one after another -- so eight stages make one block.  With G1
+// right after G0 in tensor memory, slice 0 of A meets slices 0 and 1 of B in
+// one MMA of width 2 BN (one read of A for two products).
 //
 // Output: the caller's binary64 output (written or accumulated), raw hi + lo
 // binary32 planes of the next operand (split afterwards), or, with a K split,
@@ -153,10 +155,9 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           mbar_arrive_expect_tx(&full[s], C::kStageBytes);
           const int x = kb * C::kBK;
 #pragma unroll
-          for (int pl = 0; pl < S; ++pl) {
-            uint8_t* dst = st + pl * (C::kABytes + C::kBBytes);
-            tma_load_2d(dst, &tm.a[pl], x, m0, &full[s]);
-            tma_load_2d(dst + C::kABytes, &tm.b[pl], x, n0, &full[s]);
+          for (int pl = 0; pl < S; ++pl) {  // A planes, then the B planes one after another
+            tma_load_2d(st + pl * C::kABytes, &tm.a[pl], x, m0, &full[s]);
+            tma_load_2d(st + S * C::kABytes + pl * C::kBBytes, &tm.b[pl], x, n0, &full[s]);
           }
         }
       }
@@ -167,7 +168,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     if (lane == 0) {
       // ---- MMA issuer: one accumulator pair per block ------------------------
       constexpr uint32_t idesc = make_idesc(1u, kBM, BN);
-      constexpr uint32_t kPlaneStride = C::kABytes + C::kBBytes;
+      // slice 0 of A against slices 0 and 1 of B (adjacent in the stage) in
+      // one MMA of width 2 BN, writing G0 and G1 (adjacent in tensor memory)
+      constexpr bool kMerge = C::kAccCols == BN;
+      constexpr uint32_t idesc2 = make_idesc(1u, kBM, kMerge ? 2 * BN : BN);
+      constexpr uint32_t kBBase = uint32_t(S * C::kABytes);
       uint32_t it = 0, bc = 0;  // stages consumed, blocks issued
       bool alive = true;
       for (int64_t t = blockIdx.x; t < tiles && alive; t += gridDim.x) {
@@ -198,13 +203,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
               for (int pa = 0; pa < S; ++pa) {
 #pragma unroll
                 for (int pb = 0; pb + pa < S; ++pb) {
-                  const uint32_t a_addr = s0 + pa * kPlaneStride + koff;
-                  const uint32_t b_addr = s0 + pb * kPlaneStride + C::kABytes + koff;
+                  if (kMerge && pa == 0 && pb == 1) continue;  // issued with (0,0)
+                  const uint32_t a_addr = s0 + pa * C::kABytes + koff;
+                  const uint32_t b_addr = s0 + kBBase + pb * C::kBBytes + koff;
                   // G0 takes (0,0); G1 starts with (0,1), the first other product issued
                   const bool lead = (pa == 0 && pb == 0);
                   const uint32_t acc = (first && (lead || (pa == 0 && pb == 1))) ? 0u : 1u;
-                  tc_mma<PREC_BF16>(lead ? g0 : g1, smem_desc<C::kSlab>(a_addr), smem_desc<C::kSlab>(b_addr), idesc,
-                                    acc);
+                  tc_mma<PREC_BF16>(lead ? g0 : g1, smem_desc<C::kSlab>(a_addr), smem_desc<C::kSlab>(b_addr),
+                                    lead && kMerge ? idesc2 : idesc, acc);
                 }
               }
             }

@@ -535,3 +535,33 @@ def test_library_exports_nothing_undeclared():
                          text=True).stdout
     exported = {ln.split()[-1] for ln in out.splitlines() if ln.split() and ln.split()[-1].startswith("mera_")}
     assert exported == set(_declared_symbols())
+
+
+def test_parity_growth_map_keeps_every_charge():
+    """grow._leg_map with the parity: one-to-one, and each old basis state
+    lands on a new state of the same charge (bond legs: the first ceil(dim/2)
+    states even)."""
+    from paper_1906_12030_gb300 import grow
+
+    for old, new in ((2, 3), (4, 6), (5, 8), (8, 16), (16, 32), (3, 3)):
+        mp = grow._leg_map(old, new, True)
+        assert len(set(mp)) == old and max(mp) < new
+        po, pn = I.parity_labels(old), I.parity_labels(new)
+        assert all(po[i] == pn[j] for i, j in enumerate(mp))
+        assert grow._leg_map(old, new, False) == list(range(old))
+
+
+def test_batch_lanes_put_gpu_filling_meras_in_one_lane():
+    """MERAs whose sweep fills the GPU (>= 1e13 flops: chi >= 16 here) share
+    lane 0 and run one after another; the launch-bound small ones get lanes
+    of their own while the budget lasts."""
+    chis = [8, 32, 12, 16, 24, 8, 20, 12]
+    dims = _batch_dims(chis)
+    need = _sweep_need(dims, m.PREC_BF16X3)
+    lanes, lane_bytes = m.mera_batch_lanes(dims, m.PREC_BF16X3, sum(need), max_lanes=32)
+    big = [i for i, c in enumerate(chis) if c >= 16]
+    small = [i for i, c in enumerate(chis) if c < 16]
+    assert all(lanes[i] == 0 for i in big)
+    assert sorted(lanes[i] for i in small) == list(range(1, len(small) + 1))
+    assert lane_bytes[0] == max(need[i] for i in big)
+    assert all(lane_bytes[lanes[i]] >= need[i] for i in range(len(chis)))

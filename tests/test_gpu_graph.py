@@ -145,3 +145,35 @@ def test_sweep_from_host_buffers_equals_the_device_sweep(use_graph):
         assert torch.equal(a, b)
     if graph is not None:
         graph.close()
+
+
+def test_parity_symmetric_growth_keeps_the_symmetry():
+    """grow_state(z2=True): a parity-symmetric chi = 4 MERA grown to chi = 6
+    stays isometric, keeps every tensor block-diagonal in the parity charges,
+    and holds the old tensors at their charge-preserving positions (up to the
+    small perturbation and the polar step)."""
+    from paper_1906_12030_gb300 import grow
+
+    chi0, chi1 = 4, 6
+    layers = I.init_mera(5, chi0, z2=True)
+    st = m.MeraState([torch.from_numpy(u).cuda().reshape(-1).contiguous() for u, _ in layers],
+                     [torch.from_numpy(w).cuda().contiguous() for _, w in layers],
+                     (torch.eye(chi0 ** 3, dtype=torch.float64, device="cuda") / chi0 ** 3).reshape(-1))
+    dims = I.layer_dims(chi1)
+    g = grow.grow_state(st, dims, seed=1, eps=1e-3, z2=True, bottom_parity=I.parity_labels(4, physical=True))
+    pb = I.parity_labels(4, physical=True)
+    for k, ((cb, ct), u, w) in enumerate(zip(dims, g.us, g.ws)):
+        u = u.cpu().numpy().reshape((cb,) * 4)
+        w = w.cpu().numpy().reshape(cb, cb, ct)
+        pt = I.parity_labels(ct)
+        pair = pb[:, None] ^ pb[None, :]
+        assert np.abs(u.reshape(cb * cb, -1).T @ u.reshape(cb * cb, -1) - np.eye(cb * cb)).max() < 1e-12
+        assert np.abs(w.reshape(cb * cb, -1).T @ w.reshape(cb * cb, -1) - np.eye(ct)).max() < 1e-12
+        assert np.abs(u[pair[:, :, None, None] != pair[None, None, :, :]]).max() < 1e-14
+        assert np.abs(w[pair[:, :, None] != pt[None, None, :]]).max() < 1e-14
+        pb = pt
+    # the old top-layer isometry at its charge-preserving positions
+    mb = grow._leg_map(chi0, chi1, True)
+    w_old = layers[-1][1]
+    w_new = g.ws[-1].cpu().numpy().reshape(chi1, chi1, chi1)[np.ix_(mb, mb, mb)]
+    assert np.abs(w_new - w_old).max() < 1e-2

@@ -268,7 +268,7 @@ mera_status mera_sweep_batch(mera_state* states, int n, const double* const* h1,
  * chi_b[i * n_layers + k], chi_t[i * n_layers + k]; its scratch is
  * mera_sweep_workspace_size and its cost the contraction flops of one sweep
  * with n_pow power steps.  MERAs whose sweep alone fills the GPU (at least
- * 1e13 flops, e.g. chi >= 16 with tau* = 3) all go to lane 0, one after
+ * 1e14 flops, e.g. chi >= 20 with tau* = 3) all go to lane 0, one after
  * another: their GEMMs are persistent kernels over every SM, and two of them
  * side by side only contend (measured: 0.94x of one at a time for a 32-MERA
  * mix of chi 8..32 with one lane each).  The others get longest-processing-

@@ -1184,7 +1184,9 @@ extern "C" mera_status mera_batch_lanes(int n, int n_layers, const int* chi_b, c
   std::vector<size_t> bytes;
   std::vector<double> load;
   size_t used = 0;
-  constexpr double kFillFlops = 1e13;  // a chi = 16 sweep (2.0e13) fills the GPU; chi = 12 (1.5e12) does not
+  // a chi = 20 sweep (1.2e14) is GEMM-bound throughout; a chi = 16 one (2.0e13) still has latency-bound parts
+  // (polar updates, small GEMMs) that overlap with other lanes
+  constexpr double kFillFlops = 1e14;
   size_t big_need = 0;
   double big_load = 0.0;
   for (int i = 0; i < n; ++i)

@@ -552,15 +552,15 @@ def test_parity_growth_map_keeps_every_charge():
 
 
 def test_batch_lanes_put_gpu_filling_meras_in_one_lane():
-    """MERAs whose sweep fills the GPU (>= 1e13 flops: chi >= 16 here) share
-    lane 0 and run one after another; the launch-bound small ones get lanes
-    of their own while the budget lasts."""
+    """MERAs whose sweep fills the GPU (>= 1e14 flops: chi >= 20 here) share
+    lane 0 and run one after another; the others get lanes of their own while
+    the budget lasts."""
     chis = [8, 32, 12, 16, 24, 8, 20, 12]
     dims = _batch_dims(chis)
     need = _sweep_need(dims, m.PREC_BF16X3)
     lanes, lane_bytes = m.mera_batch_lanes(dims, m.PREC_BF16X3, sum(need), max_lanes=32)
-    big = [i for i, c in enumerate(chis) if c >= 16]
-    small = [i for i, c in enumerate(chis) if c < 16]
+    big = [i for i, c in enumerate(chis) if c >= 20]
+    small = [i for i, c in enumerate(chis) if c < 20]
     assert all(lanes[i] == 0 for i in big)
     assert sorted(lanes[i] for i in small) == list(range(1, len(small) + 1))
     assert lane_bytes[0] == max(need[i] for i in big)

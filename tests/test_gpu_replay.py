@@ -1,0 +1,152 @@
+"""Plain FP64 GPU sweeps replayed by the oracle from GPU checkpoints, on the
+plain-FP64 workload (critical Ising chain, sites blocked to d = 4, two
+transitional layers and one scale-invariant layer, 20 power steps of rho*
+per sweep) at chi = 8 and chi = 16.
+
+The GPU state after k sweeps is copied out; from it the oracle runs one
+sweep (Sec. II C) and the GPU runs one FP64 sweep, and the two are compared:
+energy per spin, rho* and every updated u and w.  The first checkpoint
+follows one FP64 sweep from the seeded start; the later one follows a few
+hundred more sweeps taken in the OZ4 mode (it tracks the FP64 sweep to
+~1e-9 per spin at a small fraction of its time), which brings the MERA
+near convergence.
+
+Tolerance for an updated tensor.  Each update is -polar(Gamma) of the
+tensor's environment (Fig. 5).  To first order, a perturbation E of
+Gamma = U S V^T moves the polar factor by U K V^T, K_ij = (e_ij - e_ji) /
+(s_i + s_j) with e = U^T E V, plus (I - U U^T) E V S^-1 when Gamma is tall
+(Higham, Functions of Matrices, Sec. 8.1).  For real matrices K_ii = 0, so
+the condition number is kappa = s_1 / (s_(n-1) + s_n) for a square Gamma
+(u) and s_1 / s_n for a tall one (w).  The two sides form Gamma to ~1e-15
+relative and take its polar factor by different methods (Newton-Schulz on
+the GPU, an SVD in the oracle), so their updates may differ by ~eps kappa.
+As the MERA converges the disentanglers' environments become nearly
+singular (kappa ~ 1e13 at chi = 16 after a few hundred sweeps) and their
+updates then differ in directions that the energy does not see.  Each
+tensor is therefore held to 1e-9 + eps kappa, with kappa from the oracle's
+own environment.  Where that tolerance is used, both updates must also give
+the same value of the linearised energy tr(Gamma^T X) (the quantity the
+update minimises).  The energy and rho* are held to 1e-12.
+"""
+import numpy as np
+import pytest
+
+import mera_inputs as I
+from oracle import mera_oracle as O
+
+EPS = 2.0 ** -52
+FLOOR = 1e-9
+N_POW = 20
+
+
+def _cuda(x):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+class _OracleSweepInside:
+    """The environments the oracle's sweep formed, recomputed from its
+    inputs and outputs with its own functions: h at layer tau ascended
+    through the old tensors below it; rho above the layer is the new rho*
+    for the scale-invariant layer and the one below it, else rho* descended
+    through the new tensors of the transitional layers above; Gamma_u from
+    the old u and w, Gamma_w from the new u and the old w."""
+
+    def __init__(self, old, new, rho_star, h1):
+        self.old, self.new, self.rho_star, self.h1 = old, new, rho_star, h1
+        self._h, self._rho = {0: h1}, {}
+
+    def h(self, tau):
+        if tau not in self._h:
+            self._h[tau] = O.ascend(self.h(tau - 1), *self.old[tau - 1])
+        return self._h[tau]
+
+    def rho(self, tau):
+        n = len(self.old)
+        if tau >= n - 2:
+            return self.rho_star
+        if tau not in self._rho:
+            self._rho[tau] = O.descend(self.rho(tau + 1), *self.new[tau + 1])
+        return self._rho[tau]
+
+    def env(self, tau, which):
+        u_old, w_old = self.old[tau]
+        if which == "u":
+            return O.env_u(self.h(tau), self.rho(tau), u_old, w_old)
+        return O.env_w(self.h(tau), self.rho(tau), self.new[tau][0], w_old)
+
+
+def _polar_condition(gamma):
+    s = np.linalg.svd(gamma, compute_uv=False)
+    gap = s[-2] + s[-1] if gamma.shape[0] == gamma.shape[1] and gamma.shape[0] > 1 else s[-1]
+    return float(s[0] / gap), float(s.sum())
+
+
+def test_environments_rebuilt_from_the_oracle_sweep():
+    """The rebuilt environments are the ones the oracle's sweep used: their
+    polar updates reproduce its updated tensors bit for bit (chi = 3, after
+    a few sweeps so that every layer has moved)."""
+    h1, shift = O.ising_h1(1.0)
+    layers = I.init_mera(0, 3)
+    rho = O.identity_density(3)
+    for _ in range(3):
+        layers, rho, _ = O.sweep(layers, h1, shift, rho, N_POW)
+    new, rho_star, _ = O.sweep([(u.copy(), w.copy()) for u, w in layers], h1, shift, rho, N_POW)
+    inside = _OracleSweepInside(layers, new, rho_star, h1)
+    for tau, (u_new, w_new) in enumerate(new):
+        assert np.array_equal(O.polar_update(inside.env(tau, "u"), 2), u_new), tau
+        assert np.array_equal(O.polar_update(inside.env(tau, "w"), 2), w_new), tau
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("chi,marks", [(8, (1, 500)), (16, (1, 250))])
+def test_fp64_sweep_replayed_by_the_oracle(chi, marks):
+    torch = pytest.importorskip("torch")
+    m = pytest.importorskip("paper_1906_12030_gb300")
+    h1, shift = O.ising_h1(1.0)
+    layers = I.init_mera(0, chi)
+    shapes = [(u.shape, w.shape) for u, w in layers]
+    st = m.MeraState([_cuda(u).reshape(-1).clone() for u, _ in layers], [_cuda(w).clone() for _, w in layers],
+                     _cuda(O.identity_density(chi)).reshape(-1).clone())
+    e = torch.empty(1, dtype=torch.float64, device="cuda")
+    h1d = _cuda(h1).reshape(-1)
+    ws64 = m.workspace(m.mera_sweep_workspace_size(st.chi_b, st.chi_t, m.PREC_F64))
+    wsoz = m.workspace(m.mera_sweep_workspace_size(st.chi_b, st.chi_t, m.PREC_OZ4))
+    m.mera_device_status(clear=True)
+    done = 0
+    for mark in marks:
+        while done < mark:
+            m.mera_sweep(st, h1d, shift, N_POW, e, prec=m.PREC_F64 if done == 0 else m.PREC_OZ4,
+                         ws=ws64 if done == 0 else wsoz)
+            done += 1
+        torch.cuda.synchronize()
+        old = [(u.cpu().numpy().reshape(su), w.cpu().numpy().reshape(sw)) for (su, sw), u, w in
+               zip(shapes, st.us, st.ws)]
+        rho0 = st.rho_star.cpu().numpy().reshape((chi,) * 6)
+        # the GPU's sweep runs while the oracle's runs on the host
+        cp = m.MeraState([u.clone() for u in st.us], [w.clone() for w in st.ws], st.rho_star.clone())
+        m.mera_sweep(cp, h1d, shift, N_POW, e, prec=m.PREC_F64, ws=ws64)
+        new, rho_star, e_or = O.sweep([(u.copy(), w.copy()) for u, w in old], h1, shift, rho0, N_POW)
+        e_gpu = float(e.item())
+        assert abs(e_gpu - e_or) < 1e-12, (mark, e_gpu, e_or)
+        rho_gpu = cp.rho_star.cpu().numpy().reshape(rho_star.shape)
+        assert np.abs(rho_gpu - rho_star).max() < 1e-12 * np.abs(rho_star).max(), mark
+        inside = _OracleSweepInside(old, new, rho_star, h1)
+        for tau, ((u_or, w_or), u_d, w_d) in enumerate(zip(new, cp.us, cp.ws)):
+            cb = u_or.shape[0]
+            for which, x_or, x_d in (("u", u_or, u_d), ("w", w_or, w_d)):
+                x = x_d.cpu().numpy().reshape(x_or.shape)
+                diff = float(np.abs(x - x_or).max())
+                if diff <= FLOOR:
+                    continue
+                gamma = inside.env(tau, which).reshape(cb * cb, -1)
+                kappa, nuclear = _polar_condition(gamma)
+                xm, xo = x.reshape(gamma.shape), x_or.reshape(gamma.shape)
+                print(f"chi={chi} after {mark}: layer {tau} {which} differs by {diff:.2e}, kappa {kappa:.2e}")
+                assert diff <= FLOOR + EPS * kappa, (mark, tau, which, diff, kappa)
+                # both are isometries that minimise tr(Gamma^T X) (= -sum of Gamma's singular values)
+                assert np.abs(xm.T @ xm - np.eye(xm.shape[1])).max() < 1e-11
+                assert abs(np.sum(gamma * xm) - np.sum(gamma * xo)) <= 1e-12 * nuclear
+                assert abs(np.sum(gamma * xo) + nuclear) <= 1e-12 * nuclear
+    assert m.mera_device_status(clear=True) == 0

@@ -104,9 +104,10 @@ def _args():
                     help="--case precision: scaling dimensions (FP64 and mixed Arnoldi) of the final state")
     ap.add_argument("--ref-prec", default="f64", choices=["f64", "oz4", "oz3"],
                     help="--case precision: the mode of the reference run")
-    ap.add_argument("--spectrum-chis", default="8,16",
+    ap.add_argument("--spectrum-chis", default="4,6,8,10,12,14,16",
                     help="--case spectrum: bond dimensions of the growth ladder (parity-symmetric MERA)")
-    ap.add_argument("--spectrum-sweeps", default="6000,10000", help="--case spectrum: sweeps at each of them")
+    ap.add_argument("--spectrum-sweeps", default="4000,4000,4000,4000,4000,4000,6000",
+                    help="--case spectrum: sweeps at each of them")
     ap.add_argument("--case", default="sweep",
                     choices=["sweep", "ascend", "descend", "env_u", "env_w", "batch", "precision", "spectrum"])
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)  # internal: oracle timing child

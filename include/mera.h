@@ -177,9 +177,13 @@ mera_status mera_env_w(const double* h, const double* rho, const double* u, cons
  * Update (Fig. 5, Sec. II C): out = -polar(env) = -U V^T where the m x n
  * matrix env (row-major; rows = lower legs, columns = upper legs) has the
  * thin SVD U S V^T.  Requires m >= n >= 1.  Binary64, computed on the device
- * by the Newton-Schulz iteration X <- X (3 I - X^T X) / 2 from
- * X0 = env / ||env||_F, which converges to the polar factor for full column
- * rank.  Stops when ||X^T X - I||_F <= tol (tol <= 0 selects 1e-13 * sqrt(n))
+ * by a quintic Newton-Schulz iteration X <- X ((5/2)(I - G) + G^2), G = X^T X
+ * (every singular value x -> (5/2) x - (5/2) x^3 + x^5), from
+ * X0 = env / ||env||_F rescaled so that every singular value is at most 1;
+ * it converges quadratically to the polar factor for full column rank, and
+ * a singular value 1e-38 of the largest reaches 1 within 100 steps.  An
+ * exactly rank-deficient env has no unique polar factor: its null space stays
+ * at zero.  Stops when ||X^T X - I||_F <= tol (tol <= 0 selects 1e-13 * sqrt(n))
  * or after max_iter steps (<= 0 selects 100); in the latter case the last
  * iterate is written and bit (1 << MERA_ENOTCONV) of the device status word
  * is set (mera_device_status).  Asynchronous like every compute call: the
@@ -295,7 +299,7 @@ mera_status mera_batch_lanes(int n, int n_layers, const int* chi_b, const int* c
  *   out = polar(X - eta (G - X sym(X^T G))),  sym(A) = (A + A^T) / 2,
  * i.e. one gradient step of length eta along the Riemannian gradient of the
  * embedded metric, retracted to the manifold by the polar factor (computed
- * by the polar update's Newton-Schulz iteration).  out may alias X, not G.
+ * by the polar update's quintic Newton-Schulz iteration).  out may alias X, not G.
  * Scratch: mera_stiefel_workspace_size(m, n).  Non-convergence of the
  * retraction is reported as for mera_polar_update.
  *

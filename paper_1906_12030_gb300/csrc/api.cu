@@ -1,5 +1,5 @@
 // C ABI of the MERA library: argument checks, contraction-program execution,
-// the scale-invariant fixed point, the polar update (Newton-Schulz; a
+// the scale-invariant fixed point, the polar update (quintic Newton-Schulz; a
 // conditional while loop when recorded into a graph), the Stiefel gradient
 // step, the energy, the native sweep driver (SVD or Riemannian updates),
 // batched sweeps, recorded sweep graphs and the tile-width autotuner.
@@ -401,7 +401,7 @@ extern "C" mera_status mera_fixed_point_rho(const double* u, const double* w, in
 // Polar update.
 // ---------------------------------------------------------------------------
 static size_t polar_bytes(int m, int n) {
-  return 2 * align_up(size_t(m) * n * sizeof(double)) + 2 * align_up(size_t(n) * n * sizeof(double)) +
+  return 2 * align_up(size_t(m) * n * sizeof(double)) + 3 * align_up(size_t(n) * n * sizeof(double)) +
          kReduceBytes;
 }
 
@@ -418,15 +418,17 @@ extern "C" mera_status mera_polar_workspace_size(int m, int n, size_t* bytes) {
 }
 
 // Records the whole polar update on the capturing stream s: scaling, the
-// Newton-Schulz steps as a conditional while-loop node whose body ends with
-// a kernel that decides on the device whether to go on, the result chosen
-// on the device, and non-convergence set in the device status word.
+// quintic Newton-Schulz steps X <- X ((5/2)(I - G) + G^2), G = X^T X, as a
+// conditional while-loop node whose body ends with a kernel that decides on
+// the device whether to go on, the result chosen on the device, and
+// non-convergence set in the device status word.
 static mera_status polar_record(const double* env, int m, int n, double* out, int max_iter, double tol, void* ws,
                                 size_t ws_bytes, cudaStream_t s) {
   Arena ar{static_cast<char*>(ws), ws_bytes};
   double* X = reinterpret_cast<double*>(ar.take(size_t(m) * n * sizeof(double)));
   double* Xn = reinterpret_cast<double*>(ar.take(size_t(m) * n * sizeof(double)));
   double* G = reinterpret_cast<double*>(ar.take(size_t(n) * n * sizeof(double)));
+  double* G2 = reinterpret_cast<double*>(ar.take(size_t(n) * n * sizeof(double)));
   double* Bm = reinterpret_cast<double*>(ar.take(size_t(n) * n * sizeof(double)));
   double* red = reinterpret_cast<double*>(ar.take(kReduceBytes));
   double* scalars = red + 4096;
@@ -450,10 +452,18 @@ static mera_status polar_record(const double* env, int m, int n, double* out, in
     g.C = G; g.m_dst = row_n; g.n_dst = col_1; g.alpha = 1.0; g.accumulate = 0;
     return launch_gemm_f64(g, st);
   };
-  // One step src -> dst = src (3 I - G) / 2, ending with the next step's G.
+  // One step src -> dst = src ((5/2)(I - G) + G^2), ending with the next
+  // step's G.
   auto step = [&](const double* src, double* dst, cudaStream_t st) {
-    cudaError_t r = launch_ns_step(G, Bm, n, red, scalars + 1, tol, state, st);
+    GemmF64Args q;  // G2 = G G (skipped once converged)
+    q.skip_if = state;
+    q.A = G; q.a_m = n; q.a_k = 1;
+    q.B = G; q.b_n = 1; q.b_k = n;
+    q.M = n; q.N = n; q.K = n;
+    q.C = G2; q.m_dst = row_n; q.n_dst = col_1; q.alpha = 1.0; q.accumulate = 0;
+    cudaError_t r = launch_gemm_f64(q, st);
     if (r != cudaSuccess) return r;
+    if ((r = launch_ns_step(G, G2, Bm, n, red, scalars + 1, tol, state, st)) != cudaSuccess) return r;
     GemmF64Args g;
     g.skip_if = state;
     g.A = src; g.a_m = n; g.a_k = 1;

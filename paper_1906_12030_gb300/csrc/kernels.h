@@ -64,10 +64,11 @@ cudaError_t launch_sym_normalize(const double* X, double* rho, int64_t n, double
 cudaError_t launch_ns_prescale(double* G, double* X, int64_t m, int64_t n, double* c, cudaStream_t stream);
 cudaError_t launch_frob_scale(const double* src, double* dst, int64_t count, double* partials,
                               double* scalars, cudaStream_t stream);
-// One gated Newton-Schulz step's elementwise part: Bm = (3I - G)/2, resid =
-// ||G - I||_F, state[2] = (resid <= tol).  Skipped once state[0] is set.
-cudaError_t launch_ns_step(const double* G, double* Bm, int64_t n, double* partials, double* resid, double tol,
-                           int* state, cudaStream_t stream);
+// One gated quintic Newton-Schulz step's elementwise part: Bm = (5/2)(I - G)
+// + G2 (G2 = G G), resid = ||G - I||_F, state[2] = (resid <= tol).  Skipped
+// once state[0] is set.
+cudaError_t launch_ns_step(const double* G, const double* G2, double* Bm, int64_t n, double* partials,
+                           double* resid, double tol, int* state, cudaStream_t stream);
 // Closes a step: state[1] += 1; state[0] = state[2].  Skipped once state[0] is set.
 cudaError_t launch_ns_finish(int* state, cudaStream_t stream);
 // out = -(state[1] odd ? x1 : x0): the polar result, selected on the device.

@@ -1,6 +1,6 @@
 // Binary64 kernels: operand permute/cast, FP64 GEMM with scattered epilogue,
 // deterministic reductions (trace, Hilbert-Schmidt products, norms) and the
-// elementwise parts of the Newton-Schulz polar iteration.
+// elementwise parts of the polar iteration (quintic Newton-Schulz).
 #include <algorithm>
 #include <vector>
 
@@ -509,7 +509,7 @@ cudaError_t launch_sym_normalize(const double* X, double* rho, int64_t n, double
 }
 
 // ---------------------------------------------------------------------------
-// Polar (Newton-Schulz) helpers.
+// Polar (quintic Newton-Schulz) helpers.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) sumsq_kernel(const double* __restrict__ x, int64_t count, double* partials) {
   double v = 0.0;
@@ -581,18 +581,26 @@ cudaError_t launch_frob_scale(const double* src, double* dst, int64_t count, dou
   return cudaGetLastError();
 }
 
-// Bm = (3 I - G) / 2 and partial sums of ||G - I||_F^2.
-__global__ void __launch_bounds__(256) ns_combine_kernel(const double* __restrict__ G, double* Bm, int64_t n,
-                                                         double* partials, const int* skip_if) {
+// The step X <- X p(X^T X) with the odd quintic x p(x^2),
+//   p(g) = 5/2 - (5/2) g + g^2,  so that x p(x^2) = (5/2) x - (5/2) x^3 + x^5:
+// it fixes 1 with zero slope (x p(x^2) - 1 ~ (5/2) (x - 1)^2: quadratic
+// convergence, like the cubic (3 x - x^3) / 2), maps [0, 1] into
+// [0, 1.061], below its repelling fixed point sqrt(3/2) = 1.225, and grows a
+// small singular value 2.5-fold per step where the cubic grows it 1.5-fold.
+// At three products per step against two that is 1.36 against 1.22 per
+// product; the point is the reach of a step budget: 100 steps bring a
+// singular value of 1e-38 of the largest to 1, the cubic's 1e-17.
+// Bm = p(G) = (5/2)(I - G) + G2 (G2 = G G) and partial sums of ||G - I||_F^2.
+__global__ void __launch_bounds__(256) ns_combine_kernel(const double* __restrict__ G, const double* __restrict__ G2,
+                                                         double* Bm, int64_t n, double* partials, const int* skip_if) {
   if (skip_if && *skip_if) return;
   double v = 0.0;
   const int64_t count = n * n;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x) {
     const bool diag = (i / n) == (i % n);
-    const double g = G[i];
-    const double d = g - (diag ? 1.0 : 0.0);
+    const double d = G[i] - (diag ? 1.0 : 0.0);
     v += d * d;
-    Bm[i] = (diag ? 1.5 : 0.0) - 0.5 * g;
+    Bm[i] = fma(-2.5, d, G2[i]);
   }
   v = block_sum<256>(v);
   if (threadIdx.x == 0) partials[blockIdx.x] = v;
@@ -619,11 +627,11 @@ __global__ void ns_finish_kernel(int* state) {
   if (state[2]) state[0] = 1;
 }
 
-cudaError_t launch_ns_step(const double* G, double* Bm, int64_t n, double* partials, double* resid, double tol,
-                           int* state, cudaStream_t stream) {
+cudaError_t launch_ns_step(const double* G, const double* G2, double* Bm, int64_t n, double* partials,
+                           double* resid, double tol, int* state, cudaStream_t stream) {
   const int nb = int(std::min<int64_t>((n * n + 255) / 256, 1024));
   count_launch(2);
-  ns_combine_kernel<<<nb, 256, 0, stream>>>(G, Bm, n, partials, state);
+  ns_combine_kernel<<<nb, 256, 0, stream>>>(G, G2, Bm, n, partials, state);
   ns_check_kernel<<<1, 1024, 0, stream>>>(partials, nb, resid, tol, state);
   return cudaGetLastError();
 }

@@ -106,6 +106,29 @@ def test_polar_update_f64(mm, nn):
     assert np.abs(got.T @ got - np.eye(nn)).max() < 1e-12
 
 
+def test_polar_update_converges_over_thirty_decades():
+    """env is a signed permutation of diag(s), s from 1 down to 1e-30, so
+    its polar factor is the signed permutation itself.  The quintic step
+    grows each singular value 2.5-fold until it nears 1 (81 steps from
+    1e-30), within the default 100; the cubic (3 x - x^3) / 2 grows it
+    1.5-fold and would still be at 1e-9 after 100 steps."""
+    mm, nn = 24, 12
+    rng = np.random.default_rng(5)
+    s = 10.0 ** -np.linspace(0.0, 30.0, nn)
+    rows, cols = rng.permutation(mm)[:nn], rng.permutation(nn)
+    signs = rng.choice([-1.0, 1.0], nn)
+    env = np.zeros((mm, nn))
+    env[rows, cols] = signs * s
+    want = np.zeros((mm, nn))
+    want[rows, cols] = -signs  # the update is -polar(env)
+    out = torch.empty(mm * nn, dtype=torch.float64, device="cuda")
+    m.mera_device_status(clear=True)
+    m.mera_polar_update(_cuda(env).reshape(-1), mm, nn, out)
+    got = out.cpu().numpy().reshape(mm, nn)
+    assert m.mera_device_status(clear=True) == 0
+    assert np.abs(got - want).max() < 1e-14
+
+
 def test_polar_reports_nonconvergence_for_rank_deficient_input():
     """The polar update is asynchronous: non-convergence within max_iter
     steps is reported through the device status word, not a return code."""

@@ -19,7 +19,10 @@ pytestmark = pytest.mark.gpu
 TOL_F64 = 1e-10
 # (1, 1) and (2, 1): the degenerate bond dimensions (every leg trivial, a
 # one-state coarse leg); the rest span several tiles with ragged edges.
-DIMS = [(1, 1), (2, 1), (2, 2), (3, 3), (4, 4), (5, 5), (2, 3), (4, 6), (4, 16), (3, 8), (8, 8)]
+# the last five are layers of the bond-dimension ladder chi = 6, 10, 14, whose
+# chi^2 is not a multiple of 8 (padded operand rows)
+DIMS = [(1, 1), (2, 1), (2, 2), (3, 3), (4, 4), (5, 5), (2, 3), (4, 6), (4, 16), (3, 8), (8, 8),
+        (6, 6), (4, 10), (10, 10), (4, 14), (14, 14)]
 
 
 def _cuda(x):

@@ -123,7 +123,8 @@ def _maps(prec, chi_b, chi_t, seed):
 
 
 @pytest.mark.parametrize("prec", TC_PRECS)
-@pytest.mark.parametrize("chi_b,chi_t", [(1, 1), (2, 1), (2, 2), (3, 3), (4, 4), (5, 5), (4, 16), (8, 8), (3, 8)])
+@pytest.mark.parametrize("chi_b,chi_t", [(1, 1), (2, 1), (2, 2), (3, 3), (4, 4), (5, 5), (4, 16), (8, 8), (3, 8), (6, 6),
+                                           (10, 10), (4, 14)])
 def test_maps_mixed_precision(prec, chi_b, chi_t):
     res = _maps(prec, chi_b, chi_t, 11)
     errs = {}

@@ -279,12 +279,13 @@ mera_status mera_sweep_batch(mera_state* states, int n, const double* const* h1,
  * time-first list scheduling: taken by decreasing scratch (then cost), each
  * opens a new lane while fewer than max_lanes exist and its scratch fits in
  * what is left of budget_bytes, otherwise it joins the lane with the least
- * cost so far.
+ * cost so far among those whose scratch holds it or can grow to hold it
+ * within the budget.
  * Outputs: lane[i] in [0, *n_lanes) for every MERA, and lane_bytes[l] (room
  * for n entries) the scratch of lane l, which covers each of its members;
- * the lane_bytes sum to at most budget_bytes.  MERA_ENOMEM if the largest
- * MERA alone exceeds the budget; MERA_EINVAL for bad dimensions (the error
- * text names the MERA) or arguments.
+ * the lane_bytes sum to at most budget_bytes.  MERA_ENOMEM if a MERA fits in
+ * no lane within the budget (e.g. the largest alone exceeds it); MERA_EINVAL
+ * for bad dimensions (the error text names the MERA) or arguments.
  */
 mera_status mera_batch_lanes(int n, int n_layers, const int* chi_b, const int* chi_t, int prec, int n_pow,
                              size_t budget_bytes, int max_lanes, int* lane, int* n_lanes, size_t* lane_bytes);

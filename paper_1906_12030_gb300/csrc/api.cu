@@ -1163,8 +1163,11 @@ static double sweep_flops(int n, const int* cb, const int* ct, int n_pow) {
 // one shared lane, so those run back to back.  The others get
 // longest-processing-time-first list scheduling under a cap on the summed
 // scratch: taken by decreasing scratch size (then cost), each opens a lane
-// while lanes and budget remain, else joins the least-loaded lane, whose
-// scratch (sized by its first, largest member) already holds it.
+// while lanes and budget remain, else joins the least-loaded lane among
+// those whose scratch holds it or can grow to hold it within the budget.
+// (A lane opened by a later MERA is never smaller than it; the shared lane
+// of the GPU-filling MERAs can be, when a MERA with few flops has a large
+// transitional layer.)
 extern "C" mera_status mera_batch_lanes(int n, int n_layers, const int* chi_b, const int* chi_t, int prec, int n_pow,
                                         size_t budget_bytes, int max_lanes, int* lane, int* n_lanes,
                                         size_t* lane_bytes) {
@@ -1224,11 +1227,19 @@ extern "C" mera_status mera_batch_lanes(int n, int n_layers, const int* chi_b, c
       used += b;
       continue;
     }
-    if (bytes.empty())
-      return fail(MERA_ENOMEM, "MERA %d needs %zu bytes of scratch; the budget is %zu", i, b, budget_bytes);
-    size_t best = 0;
-    for (size_t l = 1; l < load.size(); ++l)
-      if (load[l] < load[best]) best = l;
+    size_t best = bytes.size();
+    for (size_t l = 0; l < bytes.size(); ++l) {
+      const size_t grow = b > bytes[l] ? b - bytes[l] : 0;
+      if (grow > budget_bytes - used) continue;
+      if (best == bytes.size() || load[l] < load[best]) best = l;
+    }
+    if (best == bytes.size())
+      return fail(MERA_ENOMEM, "MERA %d needs %zu bytes of scratch; no lane holds it within the budget of %zu", i,
+                  b, budget_bytes);
+    if (b > bytes[best]) {
+      used += b - bytes[best];
+      bytes[best] = b;
+    }
     lane[i] = int(best);
     load[best] += cost[size_t(i)];
   }

@@ -565,3 +565,45 @@ def test_batch_lanes_put_gpu_filling_meras_in_one_lane():
     assert sorted(lanes[i] for i in small) == list(range(1, len(small) + 1))
     assert lane_bytes[0] == max(need[i] for i in big)
     assert all(lane_bytes[lanes[i]] >= need[i] for i in range(len(chis)))
+
+
+def test_batch_lanes_shared_lane_grows_for_a_joining_mera():
+    """With n_pow = 20000 the MERA with a chi = 12 scale-invariant layer is
+    GPU-filling (lane 0) while the one with a 16 -> 8 transitional layer is
+    not, though its scratch is larger.  With one lane allowed, it joins lane
+    0, whose scratch must grow to hold it."""
+    dims = [([4, 8, 12], [8, 12, 12]), ([4, 16, 8], [16, 8, 8])]
+    need = _sweep_need(dims, m.PREC_BF16X3)
+    assert need[1] > need[0]
+    lanes, lane_bytes = m.mera_batch_lanes(dims, m.PREC_BF16X3, sum(need), max_lanes=1, n_pow=20000)
+    assert lanes == [0, 0] and lane_bytes == [need[1]]
+    with pytest.raises(m.MeraError, match="budget"):
+        m.mera_batch_lanes(dims, m.PREC_BF16X3, need[1] - 1, max_lanes=1, n_pow=20000)
+
+
+def test_batch_lanes_hold_every_member_for_random_batches():
+    """Random batches of three-layer MERAs (transitional layers that grow or
+    shrink the bond dimension), power-step counts from 20 to 20000, budgets
+    from tight to loose and one to three lanes: every lane's scratch holds
+    each of its members and the lanes fit in the budget, or the call reports
+    MERA_ENOMEM."""
+    shapes = [([4, a, b], [a, b, b]) for a in (4, 8, 12, 16) for b in (2, 4, 6, 8, 12, 16) if b <= a * a]
+    need_of = dict(zip(range(len(shapes)), _sweep_need(shapes, m.PREC_BF16X3)))
+    rng = np.random.default_rng(11)
+    checked = 0
+    for _ in range(300):
+        idx = [int(i) for i in rng.integers(0, len(shapes), int(rng.integers(2, 6)))]
+        dims = [shapes[i] for i in idx]
+        need = [need_of[i] for i in idx]
+        n_pow = int(rng.choice([20, 2000, 20000]))
+        max_lanes = int(rng.integers(1, 4))
+        budget = max(need) + int(sum(need) * rng.uniform(0.0, 1.0))
+        try:
+            lanes, lane_bytes = m.mera_batch_lanes(dims, m.PREC_BF16X3, budget, max_lanes, n_pow=n_pow)
+        except m.MeraError as e:
+            assert "budget" in str(e)
+            continue
+        assert len(lane_bytes) <= max_lanes and sum(lane_bytes) <= budget
+        assert all(lane_bytes[lanes[i]] >= need[i] for i in range(len(dims)))
+        checked += 1
+    assert checked > 200

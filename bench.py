@@ -143,9 +143,12 @@ def _job_throughput(world: int, steps: int, max_ms: float) -> float:
 
 
 def _heuristic_bn(prec: str, n: int) -> int:
-    """The planner's tile width when nothing is tuned (for reporting)."""
+    """The planner's tile width when nothing is tuned (for reporting): for
+    N > 128 the width of 256, 192, 160 with the least ceil(N / w) (128 + w)."""
     if n > 128:
-        return 128 if prec in ("bf16x6", "oz3", "oz4") else 256
+        if prec in ("bf16x6", "oz3", "oz4"):
+            return 128
+        return min((256, 192, 160), key=lambda w: (-(-n // w) * (128 + w), -w))
     return 128 if n > 64 else 64 if n > 16 else 16
 
 

@@ -1025,6 +1025,7 @@ extern "C" mera_status mera_gemm_test(int prec, const double* A, const double* B
   TcGemmArgs t;
   t.prec = prec; t.A = wa; t.a_plane_bytes = pa; t.lda = ld; t.B = wb; t.b_plane_bytes = pb; t.ldb = ld;
   t.M = M; t.N = N; t.K = K; t.c_final = true; t.C = C; t.m_dst = md; t.n_dst = nd; t.alpha = 1.0; t.accumulate = 0;
+  t.bn = tc_block_n(prec, N);  // the planner's width for this N
   return cuda_status(launch_gemm_tc(t, s), "gemm test tc");
 }
 
@@ -1281,8 +1282,7 @@ extern "C" mera_status mera_autotune(int op, int chi_b, int chi_t, int prec, dou
       const int cf = g.c_buf < 0 ? 1 : 0;
       if (g.N <= 64 || g.split > 1 || !seen.insert({g.M, g.N, g.K, cf}).second) continue;
       std::vector<int> cands = {128, 64};
-      if (g.N > 128 && prec != PREC_BF16X6 && !is_oz(prec)) cands.insert(cands.begin(), 256);
-      if (g.N <= 128) cands = {128, 64};
+      if (g.N > 128 && prec != PREC_BF16X6 && !is_oz(prec)) cands.insert(cands.begin(), {256, 192, 160});
       // the planner's own choice wins unless another width is clearly (3 %)
       // faster: single-step timings on scratch data carry noise
       const int heur = tc_block_n(prec, g.N);
@@ -1336,7 +1336,8 @@ extern "C" mera_status mera_set_tile_width(int prec, long long M, long long N, l
   if (!prec_ok(prec) || prec == PREC_F64) return fail(MERA_EINVAL, "tile widths apply to the tensor-core modes");
   if (M < 1 || N < 1 || K < 1 || (c_final != 0 && c_final != 1)) return fail(MERA_EINVAL, "bad GEMM shape");
   if (bn != 0) {
-    const bool ok = N > 128  ? (bn == 128 || bn == 64 || (bn == 256 && prec != PREC_BF16X6 && !is_oz(prec)))
+    const bool wide = prec != PREC_BF16X6 && !is_oz(prec);
+    const bool ok = N > 128  ? (bn == 128 || bn == 64 || (wide && (bn == 256 || bn == 192 || bn == 160)))
                     : N > 64 ? (bn == 128 || bn == 64)
                              : false;
     if (!ok) return fail(MERA_EINVAL, "width %d is not an autotuner candidate for N = %lld", bn, N);

@@ -25,7 +25,25 @@ int elem_bytes(int prec) {
 int tc_block_n(int prec, int64_t N) {
   // the fixed-point split modes keep two accumulators per buffer in tensor
   // memory (4 x width columns of 512): 128 at most
-  if (N > 128) return (prec == PREC_BF16X6 || is_oz(prec)) ? 128 : 256;
+  if (N > 128) {
+    if (prec == PREC_BF16X6 || is_oz(prec)) return 128;
+    // The widest tile unless a 192- or 160-wide one covers N with less
+    // padding.  The kernel is bound by shared-memory reads, which per tile
+    // are ~(128 + width) rows of K, so compare ceil(N / width) (128 + width):
+    // N = 576 (chi = 24) takes three 192-wide tiles, N = 1600 (chi = 40)
+    // keeps 256 (seven tiles, the last a quarter full, cost less than ten
+    // 160-wide ones).
+    int best = 256;
+    int64_t cost = (N + 255) / 256 * (128 + 256);
+    for (int bn : {192, 160}) {
+      const int64_t c = (N + bn - 1) / bn * (128 + bn);
+      if (c < cost) {
+        best = bn;
+        cost = c;
+      }
+    }
+    return best;
+  }
   if (N > 64) return 128;
   if (N > 16) return 64;
   return 16;

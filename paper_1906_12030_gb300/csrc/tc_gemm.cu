@@ -238,7 +238,10 @@ struct Cfg {
   static constexpr int kStages = kStageBudget / kStageBytes > 8 ? 8
                                  : (kStageBudget / kStageBytes < 2 ? 2 : kStageBudget / kStageBytes);
   static constexpr int kAccCols = BN < 32 ? 32 : BN;     // one accumulator
-  static constexpr int kTmemCols = 2 * kAccCols;            // two, double-buffered
+  // column distance of the two (double-buffered) accumulators: a power of
+  // two, as the allocation must be (160 and 192 wide tiles use 256)
+  static constexpr int kAccStride = kAccCols <= 32 ? 32 : kAccCols <= 64 ? 64 : kAccCols <= 128 ? 128 : 256;
+  static constexpr int kTmemCols = 2 * kAccStride;
   static constexpr uint32_t kFmt = (PREC == PREC_TF32) ? 2u : 1u;  // TF32 / BF16
   static constexpr size_t kSmem = 1024 + size_t(kStages) * kStageBytes + 1024 + BN * (sizeof(int64_t) + sizeof(int));
 };
@@ -381,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t b = tc & 1;
         if (tc >= 2 && !mbar_wait(&acc_empty[b], ((tc >> 1) - 1) & 1, abort_flag)) break;
         tc_fence_after();
-        const uint32_t d = tmem + b * uint32_t(C::kAccCols);
+        const uint32_t d = tmem + b * uint32_t(C::kAccStride);
         const int kb0 = int(t / tiles_mn) * ep.kc, kb1 = min(kb0 + ep.kc, num_k);
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const uint32_t s = it % C::kStages;
@@ -450,7 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], (tc >> 1) & 1, abort_flag) ? 1 : 0);
       tc_fence_after();
       if (!ok) continue;  // the next snapshot sees the abort flag
-      const uint32_t taddr = tmem + b * uint32_t(C::kAccCols) + (uint32_t(quarter * 32) << 16);
+      const uint32_t taddr = tmem + b * uint32_t(C::kAccStride) + (uint32_t(quarter * 32) << 16);
       if (ch_lo >= ch_hi) {  // no columns for this warp: hand the accumulator back at once
         tc_fence_before();
         __syncwarp();
@@ -798,6 +801,12 @@ cudaError_t launch_prec(const TcGemmArgs& a, cudaStream_t stream) {
     case 256:
       if constexpr (PREC == PREC_BF16X6) return cudaErrorInvalidValue;  // one stage only
       else return launch_cfg<PREC, 256>(a, stream);
+    case 192:  // N = 576 (chi = 24) in three full tiles
+      if constexpr (PREC == PREC_BF16X6) return cudaErrorInvalidValue;
+      else return launch_cfg<PREC, 192>(a, stream);
+    case 160:
+      if constexpr (PREC == PREC_BF16X6) return cudaErrorInvalidValue;
+      else return launch_cfg<PREC, 160>(a, stream);
     case 128: return launch_cfg<PREC, 128>(a, stream);
     case 64: return launch_cfg<PREC, 64>(a, stream);
     case 16: return launch_cfg<PREC, 16>(a, stream);

@@ -80,7 +80,7 @@ def test_reported_planner_widths_match_the_planner():
     m.mera_autotune_reset()
     for name in ("tf32", "bf16", "bf16x3", "bf16x6", "oz3", "oz4"):
         prec = m.PRECS[name]
-        for chi_b, chi_t in ((4, 16), (16, 16), (8, 8), (3, 5)):
+        for chi_b, chi_t in ((4, 16), (16, 16), (8, 8), (3, 5), (12, 12), (24, 24)):
             for op in (m.OP_ASCEND, m.OP_DESCEND, m.OP_ENV_U, m.OP_ENV_W):
                 for dg in m.mera_plan_json(op, chi_b, chi_t, prec)["diagrams"]:
                     for st in dg["steps"]:

@@ -63,8 +63,9 @@ def _device_status_clean():
 
 
 @pytest.mark.parametrize("prec", TC_PRECS + [m.PREC_F64])
-@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (16, 16, 16), (200, 300, 100), (130, 17, 7), (1000, 64, 520),
-                                   (4096, 256, 512), (257, 129, 33), (64, 512, 2048)])
+# the planner's widths for these N: 256, 16, 160 (300), 192 (576), 64, 64, 256, 160 (129), 256
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (16, 16, 16), (200, 300, 100), (300, 576, 200), (130, 17, 7),
+                                   (1000, 64, 520), (4096, 256, 512), (257, 129, 33), (64, 512, 2048)])
 def test_gemm_bound(prec, M, N, K):
     rng = np.random.default_rng(M * 7 + N * 13 + K)
     A = rng.standard_normal((M, K))
@@ -124,7 +125,7 @@ def _maps(prec, chi_b, chi_t, seed):
 
 @pytest.mark.parametrize("prec", TC_PRECS)
 @pytest.mark.parametrize("chi_b,chi_t", [(1, 1), (2, 1), (2, 2), (3, 3), (4, 4), (5, 5), (4, 16), (8, 8), (3, 8), (6, 6),
-                                           (10, 10), (4, 14)])
+                                           (10, 10), (4, 14), (4, 12), (12, 12)])
 def test_maps_mixed_precision(prec, chi_b, chi_t):
     res = _maps(prec, chi_b, chi_t, 11)
     errs = {}
